@@ -1,0 +1,347 @@
+"""Benchmark: demag-convolution + exchange + LLG/RK4 throughput on one GB300 (or N replicas).
+
+Workload (default): thin film 1024 x 1024 x 1 cells of 2 x 2 x 3 nm, Ms = 8.6e5 A/m,
+A_ex = 1.3e-11 J/m, alpha = 0.02, dt = 1e-13 s, seeded vortex + noise initial state,
+1000 RK4 steps per benchmark step (4 demag evaluations per RK4 step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+value  = cells x demag evaluations / s over the K timed steps (Gcell-demag/s), inputs resident
+         in HBM; L2 is flushed (512 MB write) before each timed step.
+e2e    = the same metric through the public API with host buffers: pinned-host m -> device,
+         gbd_llg_step, device -> pinned-host m, inside the timed region.
+Multi-GPU: the meshes are independent, so N ranks run N replicas (no collective on the data
+path); value is the sum over ranks divided by the slowest rank's time ("scaling": "weak").
+--impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the same
+workload (one RK4 step = 4 demag evaluations of the full film), rank 0 only.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-demag/s & LLG steps/s; served p50/p99 vs plain path at rel err ≤1e-5"
+UNIT = "Gcell-demag/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def film_bytes_per_launch(n, Hx, Ky):
+    """Algorithmic DRAM bytes of one launch of each film pass (FP32 data, complex64 spectra).
+
+    row_rk (x C2R + exchange + LLG + RK4 stage + next x R2C), averaged over the four stages:
+      spectrum read 8*3*Hx*ny + spectrum write 8*3*Hx*ny (the last stage of a call skips it)
+      + m_stage 12 B/cell + m0/acc reads (stages 2-4: 24 B/cell) + acc/next writes
+      (stages 1-3: 24 B/cell, stage 4: 12 B/cell): 12 + 18 + 21 = 51 B/cell on average.
+    film_conv (y FFT -> kernel product -> y IFFT): spectrum read + write 2*8*3*Hx*ny
+      + kernel 16*Hx*Ky.
+    row_fwd (x R2C of m): 12 B/cell + spectrum write 8*3*Hx*ny.
+    """
+    nx, ny, nz = n
+    N = nx * ny * nz
+    spec = 8 * 3 * Hx * ny * nz
+    return {
+        "row_rk": 2 * spec + 51 * N,
+        "film_conv": 2 * spec + 16 * Hx * Ky,
+        "row_fwd": spec + 12 * N,
+    }
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("gbd_fft.cuh", "gbd_kernels.cu", "gbd_kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_2308_08447_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernels."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    v = d.get("bytes_per_launch", {}).get(kernel)
+    return float(v) if v is not None else None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2308_08447_gb300 import gbdemag
+    from paper_2308_08447_gb300 import workloads as W
+
+    rank, world, local = _dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    gbdemag.load()
+
+    spec = W.thin_film()
+    nsteps = args.llg_steps
+    m0 = W.vortex_noise(spec.n, spec.cell, spec.seed)
+    mesh = gbdemag.Mesh(spec.n, spec.cell, spec.Ms, A_ex=spec.A_ex, alpha=spec.alpha)
+    m = torch.from_numpy(m0).cuda()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    cells = spec.cells
+    evals_per_step = 4 * nsteps
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up
+    for _ in range(args.warmup):
+        mesh.llg_step(m, nsteps, spec.dt)
+    torch.cuda.synchronize()
+
+    # timed region: K steps, L2 flushed before each, device time by CUDA events on the stream
+    sampler = ClockSampler(local)
+    sampler.start()
+    times = []
+    barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mesh.llg_step(m, nsteps, spec.dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    t_total = sum(times) / 1e3
+    if dist is not None:
+        t = torch.tensor([t_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    value = world * cells * evals_per_step * args.steps / t_total / 1e9
+    ms_per_step = t_total * 1e3 / args.steps
+
+    # end to end through the public API with host buffers
+    host_in = torch.from_numpy(m0).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    md = torch.empty_like(m)
+    e2e_times = []
+    for i in range(args.steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        md.copy_(host_in, non_blocking=True)
+        mesh.llg_step(md, nsteps, spec.dt)
+        host_out.copy_(md, non_blocking=True)
+        torch.cuda.synchronize()
+        if i > 0:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_t = sum(e2e_times)
+    if dist is not None:
+        t = torch.tensor([e2e_t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e_value = world * cells * evals_per_step * len(e2e_times) / e2e_t / 1e9
+    assert np.isfinite(host_out.numpy()).all()
+
+    # per-pass device time (CUDA events around every launch), one instrumented step
+    gbdemag.gbd_mesh_set_timing(mesh.handle, True)
+    flush.zero_()
+    mesh.llg_step(m, nsteps, spec.dt)
+    torch.cuda.synchronize()
+    passes = gbdemag.gbd_mesh_read_timing(mesh.handle)
+    gbdemag.gbd_mesh_set_timing(mesh.handle, False)
+    dims = gbdemag.gbd_plan_dims(mesh.desc)
+    bpl = film_bytes_per_launch(spec.n, dims[3], dims[4])
+    top = max(passes, key=lambda k: passes[k][0])
+    avg_ms = passes[top][0] / passes[top][1]
+    peak, peak_kind = measured_peaks()
+    achieved = bpl[top] / (avg_ms * 1e-3) / 1e9
+    launches_per_step = sum(c for _, c in passes.values())
+    roofline = {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": ncu_traffic(top), "algorithmic_bytes_per_launch": bpl[top],
+                "avg_launch_us": round(avg_ms * 1e3, 2),
+                "passes_us": {k: round(v[0] / v[1] * 1e3, 2) for k, v in passes.items()},
+                "share": {k: round(v[0] / sum(x[0] for x in passes.values()), 3) for k, v in passes.items()}}
+
+    result = None
+    if rank == 0:
+        result = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "llg_steps_per_s": round(world * nsteps * args.steps / t_total, 1),
+            "config": {"workload": "thin film 1024x1024x1, 2x2x3 nm cells, demag + exchange + LLG RK4, "
+                                   "%d RK4 steps per benchmark step" % nsteps,
+                       "cells_per_gpu": cells, "demag_evals_per_step": evals_per_step, "dt_s": spec.dt,
+                       "parallelism": "replicas x%d" % world, "l2": "flushed (512 MB write) before each step"},
+            "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": host_in.numel() * 4,
+                    "d2h_bytes_per_step": host_out.numel() * 4},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+            "roofline": roofline,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            result["cpu_baseline"] = cpu_baseline(spec, m0)
+    mesh.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return result
+
+
+def cpu_baseline(spec, m0, repeats=1):
+    """The FP64 oracle, as it stands, on the host cores: `repeats` RK4 steps of the full film
+    (4 FFT-convolution demag evaluations each). Tensor set-up is outside the timed region."""
+    import numpy as np
+
+    from oracle import llg as L
+    from oracle import tensor as T
+
+    Nf = T.tensor_all_offsets(spec.n, spec.cell)
+    m = m0.astype(np.float64)
+    f = lambda v: L.rhs(v, Nf, spec.cell, spec.Ms, spec.A_ex, spec.alpha)
+    t0 = time.perf_counter()
+    for _ in range(repeats):
+        m = L.rk4_step(m, spec.dt, f)
+    t = time.perf_counter() - t0
+    value = spec.cells * 4 * repeats / t / 1e9
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d RK4 step(s) of the 1024x1024x1 film = %d demag evaluations (numpy FP64, "
+                      "single-threaded FFT); %.1f s" % (repeats, 4 * repeats, t)}
+
+
+def run_reference(args):
+    rank, world, local = _dist_env()
+    if rank != 0:
+        return None
+    from paper_2308_08447_gb300 import workloads as W
+    spec = W.thin_film()
+    m0 = W.vortex_noise(spec.n, spec.cell, spec.seed)
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; set-up (tensor) is excluded from timing
+    vals = []
+    cb = None
+    for _ in range(args.steps):
+        cb = cpu_baseline(spec, m0)
+        vals.append(cb["value"])
+    value = statistics.mean(vals)
+    cb["value"] = value
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "thin film 1024x1024x1, 2x2x3 nm cells, demag + exchange + LLG RK4; "
+                                   "each step one RK4 step (4 demag evaluations) of the FP64 CPU oracle"},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--llg-steps", type=int, default=1000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        res = run_reference(args)
+    else:
+        res = run_ours(args)
+    if res is not None:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,143 @@
+/*
+ * gbdemag -- demagnetizing-field FFT convolution and exchange + LLG/RK4 time stepping
+ * for finite-difference micromagnetics on one GB300 (sm_103a).
+ *
+ * The operation (Lepadatu, "Accelerating micromagnetic and atomistic simulations using
+ * multiple GPUs", Sec. II, Eq. 1):  H_d,i = - sum_j N(i - j) M_j  over all cells j of an
+ * nx x ny x nz mesh of identical rectangular cells, with N the cell-averaged demagnetizing
+ * tensor. It is evaluated as a zero-padded FFT convolution (Sec. II; the single-GPU steps
+ * of Appendix A): pad M to (2nx, 2ny, 2nz) -- no padding along a dimension of size 1 --,
+ * x real-to-complex FFT, y and z FFTs, pointwise product with the transformed tensor stored
+ * as its 6 real symmetry-packed components, inverse FFTs, crop. The time integrator adds
+ * the exchange field H_ex = 2A/(mu0 Ms) lap(m) (Sec. III, Eq. 4) and a uniform applied
+ * field, and advances the LLG equation (Eq. 5) with classic RK4 (Sec. III), recomputing
+ * the demag field at every stage.
+ *
+ * Conventions
+ *   - Units are SI: metres, A/m, J/m, seconds; mu0 = 4 pi 1e-7.
+ *   - Field arrays are float32, planar ("SoA"), shape [3][nz][ny][nx] (x fastest),
+ *     components (x, y, z). M and H_d are in A/m; m is the unit magnetization M / Ms.
+ *   - Device pointers are CUDA device (or managed) addresses on the current device, at
+ *     least 4-byte aligned, owned by the caller. The library never frees them.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Compute calls only enqueue
+ *     work on it and return; results are ready when the stream has reached them.
+ *   - Every call returns a gbd_status. No call aborts, throws or prints. On failure
+ *     gbd_last_error() gives a message (per calling thread). Argument errors are detected
+ *     before any work is enqueued. A CUDA error raised by enqueued work surfaces as
+ *     GBD_ECUDA from a later call on the same device (CUDA errors are sticky).
+ *   - Boundaries are free: no periodic images, and the exchange Laplacian replaces a
+ *     missing neighbour by the cell itself (Neumann).
+ */
+#ifndef GBDEMAG_H
+#define GBDEMAG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GBD_OK = 0,
+  GBD_EINVAL = 1,       /* bad argument: sizes, cell, material, NULL or misaligned pointer */
+  GBD_ENOMEM = 2,       /* device or host allocation failed */
+  GBD_ECUDA = 3,        /* a CUDA call failed (launch error, sticky fault, wrong device) */
+  GBD_ESTATE = 4,       /* call order: e.g. gbd_demag before gbd_set_kernel */
+  GBD_ETIMEOUT = 5,     /* a bounded device-side wait gave up (batched path) */
+  GBD_EBUDGET = 6,      /* admission refused: the request does not fit the memory budget */
+  GBD_EUNSUPPORTED = 7  /* mesh larger than the supported padded lengths */
+} gbd_status;
+
+/* Arithmetic of the FFT stages. FP32 is the default path. */
+typedef enum { GBD_FP32 = 0, GBD_SPLIT_BF16 = 1, GBD_SPLIT_FP16 = 2 } gbd_precision;
+
+/* Mesh and material. Sizes: 1 <= nx <= 4096, 1 <= ny <= 2048, 1 <= nz <= 2048. */
+typedef struct {
+  int nx, ny, nz;        /* cells along x, y, z */
+  double dx, dy, dz;     /* cell size, m (> 0) */
+  double Ms;             /* saturation magnetization, A/m (> 0) */
+  double A_ex;           /* exchange stiffness, J/m (>= 0; Eq. 4) */
+  double alpha;          /* Gilbert damping (>= 0; Eq. 5) */
+  double gamma;          /* gyromagnetic ratio mu0*gamma_e, m/(A s); 0 selects 2.212761569e5 */
+  double Hext[3];        /* uniform applied (Zeeman) field, A/m */
+  int precision;         /* gbd_precision */
+  unsigned flags;        /* reserved, 0 */
+} gbd_mesh_desc;
+
+typedef struct gbd_mesh gbd_mesh; /* opaque: plan, kernel spectrum, scratch, RK4 state */
+
+/* Validates desc, plans the padded lengths (powers of two >= 2n - 1; 1 where n = 1) and
+ * allocates the mesh's device buffers on the current device: x spectrum, 3D y spectrum,
+ * kernel spectrum, RK4 scratch, twiddle table. *out receives the mesh (NULL on failure).
+ * Errors: GBD_EINVAL, GBD_EUNSUPPORTED, GBD_ENOMEM, GBD_ECUDA. */
+gbd_status gbd_mesh_create(const gbd_mesh_desc* desc, gbd_mesh** out);
+
+/* Device bytes gbd_mesh_create would allocate for desc (for admission control). Host only. */
+gbd_status gbd_mesh_bytes(const gbd_mesh_desc* desc, size_t* out);
+
+/* Computes the demag tensor (Eq. 1) in FP64 on the host -- closed-form Newell stencil in
+ * the near field, Gauss-Legendre cell-pair quadrature beyond 8 cell sizes --, transforms
+ * it in FP64, folds in -1/(Px Py Pz), packs the stored quadrant (Appendix A's convolution
+ * kernel, (nx+1)(ny+1)(nz+1)-sized up to padding) and copies it to the device in FP32.
+ * Blocks until the copy is done. Must precede the compute calls. */
+gbd_status gbd_set_kernel(gbd_mesh* mesh, void* stream);
+
+/* H = H_d(M) of Eq. 1. M, H: device [3][nz][ny][nx] float32, A/m; M and H must not overlap. */
+gbd_status gbd_demag(gbd_mesh* mesh, const float* M, float* H, void* stream);
+
+/* H = Ms * H_d(m) + H_ex(m) + Hext (Sec. III: H_eff without anisotropy). m: unit vectors. */
+gbd_status gbd_effective_field(gbd_mesh* mesh, const float* m, float* H, void* stream);
+
+/* dmdt = -gamma/(1+alpha^2) [m x H_eff + alpha m x (m x H_eff)] (Eq. 5 solved for dm/dt). */
+gbd_status gbd_llg_rhs(gbd_mesh* mesh, const float* m, float* dmdt, void* stream);
+
+/* Advances m in place by nsteps classic RK4 steps of size dt (s > 0): four demag + exchange
+ * + LLG evaluations per step, stage inputs not renormalized, m renormalized at the end of
+ * each step. m: device [3][nz][ny][nx] float32 unit vectors. nsteps = 0 is a no-op. */
+gbd_status gbd_llg_step(gbd_mesh* mesh, float* m, int nsteps, double dt, void* stream);
+
+/* Frees the mesh's device buffers (after synchronizing the device). NULL is accepted. */
+gbd_status gbd_mesh_destroy(gbd_mesh* mesh);
+
+/* Message of the calling thread's last failure ("" if none). Valid until its next call. */
+const char* gbd_last_error(void);
+
+/* ---- per-pass timing ------------------------------------------------------------------- */
+
+/* Pass classes reported by gbd_mesh_read_timing. */
+enum {
+  GBD_PASS_ROW_FWD = 0,    /* x real-to-complex of an input field */
+  GBD_PASS_ROW_INV = 1,    /* x complex-to-real + crop with a field / dm/dt epilogue */
+  GBD_PASS_ROW_RK = 2,     /* x complex-to-real + exchange + LLG + RK4 stage (+ next forward) */
+  GBD_PASS_FILM_CONV = 3,  /* y FFT -> kernel product -> y IFFT (nz = 1) */
+  GBD_PASS_Y_FWD = 4,      /* 3D y FFT */
+  GBD_PASS_Z_CONV = 5,     /* 3D z FFT -> kernel product -> z IFFT */
+  GBD_PASS_Y_INV = 6,      /* 3D y IFFT + crop */
+  GBD_NPASS = 8
+};
+
+/* enable != 0: every later launch of this mesh is bracketed by two CUDA events on its
+ * stream (profiling only; it adds event records between launches). */
+gbd_status gbd_mesh_set_timing(gbd_mesh* mesh, int enable);
+
+/* Waits for the recorded events, writes per pass class the summed device time in ms and
+ * the launch count (arrays of GBD_NPASS), and clears the record. */
+gbd_status gbd_mesh_read_timing(gbd_mesh* mesh, double* ms, long long* launches);
+
+/* ---- host-only helpers (no GPU needed) ------------------------------------------------ */
+
+/* The FP64 tensor components (xx, yy, zz, xy, xz, yz) at integer cell offset (X, Y, Z). */
+gbd_status gbd_tensor_at(const gbd_mesh_desc* desc, int X, int Y, int Z, double out[6]);
+
+/* Plan of desc: out = {Px, Py, Pz, Hx, Ky, Kz} with Hx = Px/2+1 and K_d = P_d/2+1 (1 if P_d = 1). */
+gbd_status gbd_plan_dims(const gbd_mesh_desc* desc, int out[6]);
+
+/* The FP64 packed kernel spectrum that gbd_set_kernel uploads (before rounding to FP32),
+ * layout [6][Kz][Ky][Hx]; count must equal 6*Kz*Ky*Hx. Components xz, yz are zero when nz = 1. */
+gbd_status gbd_kernel_spectrum_host(const gbd_mesh_desc* desc, double* out, size_t count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBDEMAG_H */

@@ -1,0 +1,43 @@
+// Padded lengths and block shapes of one mesh's demag convolution.
+#pragma once
+#include <cstddef>
+#include <vector>
+
+namespace gbd {
+
+// Largest supported padded length along any axis; it bounds the shared-memory lines
+// (3 components x P complex values) and the twiddle table.
+constexpr int kMaxPad = 4096;
+constexpr int kMaxPadX = 8192;
+
+struct Plan {
+  int nx = 0, ny = 0, nz = 0;
+  long long N = 0;
+  // Padded periods. Sec. II pads to 2n; any P_d >= 2 n_d - 1 gives the same cropped result,
+  // and a power of two is taken. Px >= 2 so that the half-length x transform exists;
+  // Py = 1 (Pz = 1) when ny = 1 (nz = 1): no padding along a dimension of size 1.
+  int Px = 0, Py = 0, Pz = 0;
+  int Lx = 0, Hx = 0;   // Lx = Px / 2, Hx = Lx + 1 stored x frequencies
+  int Ky = 0, Kz = 0;   // stored y / z kernel frequencies: P/2 + 1 (1 when P = 1)
+  bool film = false;    // nz == 1: 3-pass path
+  // block shapes
+  int RB = 1;           // rows per x-row block
+  int Cf = 1;           // columns per film-conv block
+  int Cy = 1;           // lines per y-pass block
+  int Wz = 1;           // columns per z-conv block
+  // device bytes of each buffer
+  size_t bytes_S = 0, bytes_T = 0, bytes_K = 0, bytes_state = 0, bytes_tw = 0;
+  size_t total_bytes() const { return bytes_S + bytes_T + bytes_K + bytes_state + bytes_tw; }
+};
+
+// Fills p from the mesh size; returns false (with a message) when the mesh is out of range.
+bool make_plan(int nx, int ny, int nz, Plan& p, const char** why);
+
+}  // namespace gbd
+
+namespace gbdt {
+void newell_closed_form(double X, double Y, double Z, double dx, double dy, double dz, double out[6]);
+void dipole_quadrature(double X, double Y, double Z, double dx, double dy, double dz, int G, double out[6]);
+void tensor_at(int X, int Y, int Z, double dx, double dy, double dz, double out[6]);
+bool kernel_spectrum(const gbd::Plan& p, double dx, double dy, double dz, std::vector<double>& out);
+}  // namespace gbdt

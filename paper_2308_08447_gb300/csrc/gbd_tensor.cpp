@@ -1,0 +1,283 @@
+// Host FP64 demag tensor and its packed convolution-kernel spectrum.
+//
+// Eq. 1 (Sec. II) uses the cell-averaged demagnetizing tensor of two uniformly
+// magnetized rectangular cells (the formulas the paper cites, Newell, Williams and
+// Dunlop 1993). N(R) = (1/V) int_i int_j K(r - r') with the point-dipole kernel
+// K(r) = (I - 3 r r^T / r^2) / (4 pi r^3).
+//
+// * |R| < 8 d_max: closed form, a 27-point second-difference stencil (weights 2, -1, -1 per
+//   axis) of the antiderivatives f (diagonal) and g (off-diagonal), over 4 pi dx dy dz.
+// * |R| >= 8 d_max: the FP64 stencil loses digits to cancellation there, so the same
+//   integral is taken by quadrature over the overlap u of the two cells,
+//   N(R) = int prod_d (1 - |u_d| / d_d) K(R + u) du, split at u_d = 0 with G Gauss-Legendre
+//   nodes per half axis: G = 4 below 16 d_max, 3 below 64 d_max, 2 beyond (within 2e-8 of
+//   the exact value relative to V / (4 pi |R|^3)).
+//
+// Kernel spectrum (Sec. II, the "convolution kernel" of Appendix A): the tensor is placed
+// on the periodic P grid at X mod P_d for |X_d| <= n_d - 1 and transformed. Each component
+// is even or odd along each axis (xx, yy, zz even; xy odd in x, y; xz odd in x, z; yz odd
+// in y, z), so along each axis the transform reduces to
+//   G[k] = sum_{X >= 0} w_X N(X) cos(2 pi k X / P)   (even),  w_0 = 1, w_{X>0} = 2,
+//   G[k] = sum_{X >= 0} w_X N(X) sin(2 pi k X / P)   (odd; the full transform is -i G),
+// every component's spectrum is real, and only k_d in [0, P_d / 2] is stored. With the
+// Eq. 1 minus sign and the 1/(Px Py Pz) of the unnormalised inverse folded in:
+//   K~ = -G_x G_y G_z / (Px Py Pz) for xx, yy, zz and +G_x G_y G_z / (Px Py Pz) for xy, xz, yz.
+// Each G is computed with a complex FFT of the symmetric extension of the line.
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
+#include "gbd_plan.h"
+
+namespace gbdt {
+
+static const double PI = 3.14159265358979323846264338327950288;
+
+static inline double asinh_ratio(double num, double den) { return den > 0.0 ? std::asinh(num / den) : 0.0; }
+static inline double atan_ratio(double num, double den) { return den > 0.0 ? std::atan(num / den) : 0.0; }
+
+// f for N_xx on |x|, |y|, |z|; terms whose prefactor vanishes at 0/0 are dropped.
+static double newell_f(double x, double y, double z) {
+  x = std::fabs(x);
+  y = std::fabs(y);
+  z = std::fabs(z);
+  const double x2 = x * x, y2 = y * y, z2 = z * z;
+  const double R = std::sqrt(x2 + y2 + z2);
+  double t = 0.0;
+  if (y > 0.0) t += 0.5 * y * (z2 - x2) * asinh_ratio(y, std::sqrt(x2 + z2));
+  if (z > 0.0) t += 0.5 * z * (y2 - x2) * asinh_ratio(z, std::sqrt(x2 + y2));
+  if (x > 0.0) t -= x * y * z * atan_ratio(y * z, x * R);
+  t += (2.0 * x2 - y2 - z2) * R / 6.0;
+  return t;
+}
+
+// g for N_xy: g(|x|, |y|, |z|) * sign(x) * sign(y).
+static double newell_g(double x, double y, double z) {
+  const double s = (x > 0 ? 1.0 : (x < 0 ? -1.0 : 0.0)) * (y > 0 ? 1.0 : (y < 0 ? -1.0 : 0.0));
+  if (s == 0.0) return 0.0;
+  x = std::fabs(x);
+  y = std::fabs(y);
+  z = std::fabs(z);
+  const double x2 = x * x, y2 = y * y, z2 = z * z;
+  const double R = std::sqrt(x2 + y2 + z2);
+  double t = 0.0;
+  t += x * y * z * asinh_ratio(z, std::sqrt(x2 + y2));
+  t += y / 6.0 * (3.0 * z2 - y2) * asinh_ratio(x, std::sqrt(y2 + z2));
+  t += x / 6.0 * (3.0 * z2 - x2) * asinh_ratio(y, std::sqrt(x2 + z2));
+  if (z > 0.0) {
+    t -= z2 * z / 6.0 * atan_ratio(x * y, z * R);
+    t -= z * y2 / 2.0 * atan_ratio(x * z, y * R);
+    t -= z * x2 / 2.0 * atan_ratio(y * z, x * R);
+  }
+  t -= x * y * R / 3.0;
+  return s * t;
+}
+
+typedef double (*AntiDer)(double, double, double);
+
+static double stencil27(AntiDer F, double X, double Y, double Z, double dx, double dy, double dz) {
+  static const double w[3] = {-1.0, 2.0, -1.0};
+  double acc = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      for (int k = 0; k < 3; ++k)
+        acc += w[i] * w[j] * w[k] * F(X + (i - 1) * dx, Y + (j - 1) * dy, Z + (k - 1) * dz);
+  return acc / (4.0 * PI * dx * dy * dz);
+}
+
+void newell_closed_form(double X, double Y, double Z, double dx, double dy, double dz, double out[6]) {
+  out[0] = stencil27(newell_f, X, Y, Z, dx, dy, dz);
+  out[1] = stencil27(newell_f, Y, X, Z, dy, dx, dz);
+  out[2] = stencil27(newell_f, Z, Y, X, dz, dy, dx);
+  out[3] = stencil27(newell_g, X, Y, Z, dx, dy, dz);
+  out[4] = stencil27(newell_g, X, Z, Y, dx, dz, dy);
+  out[5] = stencil27(newell_g, Y, Z, X, dy, dz, dx);
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] for G = 2, 3, 4.
+static void gauss_legendre(int G, double* x, double* w) {
+  if (G == 2) {
+    x[0] = -1.0 / std::sqrt(3.0);
+    x[1] = -x[0];
+    w[0] = w[1] = 1.0;
+  } else if (G == 3) {
+    x[0] = -std::sqrt(0.6);
+    x[1] = 0.0;
+    x[2] = -x[0];
+    w[0] = w[2] = 5.0 / 9.0;
+    w[1] = 8.0 / 9.0;
+  } else {
+    const double a = std::sqrt(3.0 / 7.0 - 2.0 / 7.0 * std::sqrt(1.2));
+    const double b = std::sqrt(3.0 / 7.0 + 2.0 / 7.0 * std::sqrt(1.2));
+    const double wa = (18.0 + std::sqrt(30.0)) / 36.0, wb = (18.0 - std::sqrt(30.0)) / 36.0;
+    x[0] = -b; w[0] = wb;
+    x[1] = -a; w[1] = wa;
+    x[2] = a;  w[2] = wa;
+    x[3] = b;  w[3] = wb;
+  }
+}
+
+void dipole_quadrature(double X, double Y, double Z, double dx, double dy, double dz, int G, double out[6]) {
+  double xg[4], wg[4];
+  gauss_legendre(G, xg, wg);
+  // Rule for int_{-1}^{1} (1 - |s|) h(s) ds: nodes s = +-(x+1)/2, weights w/2 (1 - |s|).
+  double s[8], ws[8];
+  for (int i = 0; i < G; ++i) {
+    const double u = 0.5 * (xg[i] + 1.0);
+    s[i] = -u;
+    s[G + i] = u;
+    ws[i] = ws[G + i] = 0.5 * wg[i] * (1.0 - u);
+  }
+  const double V = dx * dy * dz;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int a = 0; a < 2 * G; ++a) {
+    const double rx = X + s[a] * dx;
+    for (int b = 0; b < 2 * G; ++b) {
+      const double ry = Y + s[b] * dy;
+      for (int c = 0; c < 2 * G; ++c) {
+        const double rz = Z + s[c] * dz;
+        const double r2 = rx * rx + ry * ry + rz * rz;
+        const double r = std::sqrt(r2);
+        const double pre = ws[a] * ws[b] * ws[c] / (r2 * r);
+        const double q = 3.0 / r2;
+        acc[0] += pre * (1.0 - q * rx * rx);
+        acc[1] += pre * (1.0 - q * ry * ry);
+        acc[2] += pre * (1.0 - q * rz * rz);
+        acc[3] -= pre * q * rx * ry;
+        acc[4] -= pre * q * rx * rz;
+        acc[5] -= pre * q * ry * rz;
+      }
+    }
+  }
+  for (int i = 0; i < 6; ++i) out[i] = acc[i] * V / (4.0 * PI);
+}
+
+void tensor_at(int X, int Y, int Z, double dx, double dy, double dz, double out[6]) {
+  const double px = X * dx, py = Y * dy, pz = Z * dz;
+  const double dmax = std::fmax(dx, std::fmax(dy, dz));
+  const double r = std::sqrt(px * px + py * py + pz * pz) / dmax;
+  if (r < 8.0)
+    newell_closed_form(px, py, pz, dx, dy, dz, out);
+  else
+    dipole_quadrature(px, py, pz, dx, dy, dz, r < 16.0 ? 4 : (r < 64.0 ? 3 : 2), out);
+}
+
+// ---- FP64 host FFT (radix-2, in place) -------------------------------------------------------
+struct Fft1 {
+  int n = 0, logn = 0;
+  std::vector<std::complex<double>> w;
+  std::vector<int> rev;
+  explicit Fft1(int n_) : n(n_) {
+    while ((1 << logn) < n) ++logn;
+    w.resize(n / 2 > 0 ? n / 2 : 1);
+    for (int k = 0; k < n / 2; ++k) w[k] = std::polar(1.0, -2.0 * PI * k / n);
+    rev.resize(n);
+    for (int i = 0; i < n; ++i) {
+      int r = 0;
+      for (int b = 0; b < logn; ++b)
+        if (i & (1 << b)) r |= 1 << (logn - 1 - b);
+      rev[i] = r;
+    }
+  }
+  void forward(std::complex<double>* a) const {
+    for (int i = 0; i < n; ++i)
+      if (i < rev[i]) std::swap(a[i], a[rev[i]]);
+    for (int len = 2; len <= n; len <<= 1) {
+      const int step = n / len;
+      for (int i = 0; i < n; i += len)
+        for (int j = 0; j < len / 2; ++j) {
+          std::complex<double> u = a[i + j], v = a[i + j + len / 2] * w[j * step];
+          a[i + j] = u + v;
+          a[i + j + len / 2] = u - v;
+        }
+    }
+  }
+};
+
+// G[k], k in [0, H), of the line v[X], X in [0, n), with the given parity on a period P.
+static void line_transform(const Fft1* fft, int P, int n, int H, int parity, const double* v, long long vstride,
+                           double* out, long long ostride, std::vector<std::complex<double>>& buf) {
+  if (P == 1) {
+    out[0] = v[0];
+    return;
+  }
+  std::fill(buf.begin(), buf.end(), std::complex<double>(0.0, 0.0));
+  buf[0] = v[0];
+  for (int X = 1; X < n; ++X) {
+    const double val = v[X * vstride];
+    buf[X] = val;
+    buf[P - X] = parity > 0 ? val : -val;
+  }
+  fft->forward(buf.data());
+  for (int k = 0; k < H; ++k) out[k * ostride] = parity > 0 ? buf[k].real() : -buf[k].imag();
+}
+
+static const int PARITY[6][3] = {{1, 1, 1}, {1, 1, 1}, {1, 1, 1}, {-1, -1, 1}, {-1, 1, -1}, {1, -1, -1}};
+
+// Packed spectrum, FP64, layout [6][Kz][Ky][Hx] with Hx = Px/2+1, Ky = Py/2+1 (1 if Py = 1),
+// Kz likewise. Returns false on allocation failure.
+bool kernel_spectrum(const gbd::Plan& p, double dx, double dy, double dz, std::vector<double>& out) {
+  const int nx = p.nx, ny = p.ny, nz = p.nz;
+  const long long Noct = (long long)nx * ny * nz;
+  std::vector<double> oct;
+  try {
+    oct.resize((size_t)Noct * 6);
+    out.assign((size_t)6 * p.Kz * p.Ky * p.Hx, 0.0);
+  } catch (...) {
+    return false;
+  }
+#pragma omp parallel for schedule(dynamic, 64)
+  for (long long i = 0; i < Noct; ++i) {
+    const int X = (int)(i % nx), Y = (int)((i / nx) % ny), Z = (int)(i / ((long long)nx * ny));
+    double v[6];
+    tensor_at(X, Y, Z, dx, dy, dz, v);
+    for (int c = 0; c < 6; ++c) oct[(size_t)c * Noct + i] = v[c];
+  }
+  Fft1 fx(p.Px), fy(p.Py), fz(p.Pz);
+  const double scale = 1.0 / ((double)p.Px * p.Py * p.Pz);
+  const int ncomp = (p.nz == 1) ? 4 : 6;  // xz, yz vanish identically in a single-layer mesh
+  for (int c = 0; c < ncomp; ++c) {
+    const double* src = oct.data() + (size_t)c * Noct;
+    // x: [Z][Y][X] -> A1 [Z][Y][kx]
+    std::vector<double> A1((size_t)nz * ny * p.Hx);
+#pragma omp parallel
+    {
+      std::vector<std::complex<double>> buf(p.Px);
+#pragma omp for
+      for (long long l = 0; l < (long long)nz * ny; ++l)
+        line_transform(&fx, p.Px, nx, p.Hx, PARITY[c][0], src + l * nx, 1, A1.data() + l * p.Hx, 1, buf);
+    }
+    // y: A1 [Z][Y][kx] -> A2 [Z][ky][kx]
+    std::vector<double> A2((size_t)nz * p.Ky * p.Hx);
+#pragma omp parallel
+    {
+      std::vector<std::complex<double>> buf(p.Py);
+#pragma omp for
+      for (long long l = 0; l < (long long)nz * p.Hx; ++l) {
+        const long long Z = l / p.Hx, kx = l % p.Hx;
+        line_transform(&fy, p.Py, ny, p.Ky, PARITY[c][1], A1.data() + Z * ny * p.Hx + kx, p.Hx,
+                       A2.data() + Z * p.Ky * p.Hx + kx, p.Hx, buf);
+      }
+    }
+    A1.clear();
+    A1.shrink_to_fit();
+    // z: A2 [Z][ky][kx] -> out [kz][ky][kx], scaled and signed
+    double* dst = out.data() + (size_t)c * p.Kz * p.Ky * p.Hx;
+    const double sgn = (c < 3) ? -scale : scale;
+    const long long plane = (long long)p.Ky * p.Hx;
+#pragma omp parallel
+    {
+      std::vector<std::complex<double>> buf(p.Pz);
+      std::vector<double> tmp(p.Kz);
+#pragma omp for
+      for (long long l = 0; l < plane; ++l) {
+        line_transform(&fz, p.Pz, nz, p.Kz, PARITY[c][2], A2.data() + l, plane, tmp.data(), 1, buf);
+        for (int kz = 0; kz < p.Kz; ++kz) dst[kz * plane + l] = sgn * tmp[kz];
+      }
+    }
+  }
+  return true;
+}
+
+}  // namespace gbdt

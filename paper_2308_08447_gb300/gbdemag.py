@@ -1,0 +1,233 @@
+"""Python binding of libgbdemag.so (the C ABI declared in include/gbdemag.h).
+
+Argument marshalling only: every step of the demag convolution and of the LLG/RK4
+update runs in the library's CUDA kernels. PyTorch supplies device memory and
+streams: field arguments are contiguous float32 CUDA tensors of shape
+(3, nz, ny, nx), and ``stream`` defaults to torch's current stream.
+
+There is no fallback: if the shared library has not been built, ``load()`` raises.
+"""
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgbdemag.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "gbdemag.h")
+
+GBD_OK, GBD_EINVAL, GBD_ENOMEM, GBD_ECUDA, GBD_ESTATE, GBD_ETIMEOUT, GBD_EBUDGET, GBD_EUNSUPPORTED = range(8)
+STATUS_NAMES = {0: "GBD_OK", 1: "GBD_EINVAL", 2: "GBD_ENOMEM", 3: "GBD_ECUDA", 4: "GBD_ESTATE",
+                5: "GBD_ETIMEOUT", 6: "GBD_EBUDGET", 7: "GBD_EUNSUPPORTED"}
+GBD_FP32, GBD_SPLIT_BF16, GBD_SPLIT_FP16 = 0, 1, 2
+
+
+class GbdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class gbd_mesh_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("Ms", ctypes.c_double), ("A_ex", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("Hext", ctypes.c_double * 3),
+                ("precision", ctypes.c_int), ("flags", ctypes.c_uint)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SIG = {
+    "gbd_mesh_create": [ctypes.POINTER(gbd_mesh_desc), ctypes.POINTER(_P)],
+    "gbd_mesh_bytes": [ctypes.POINTER(gbd_mesh_desc), ctypes.POINTER(ctypes.c_size_t)],
+    "gbd_set_kernel": [_P, _P],
+    "gbd_demag": [_P, _P, _P, _P],
+    "gbd_effective_field": [_P, _P, _P, _P],
+    "gbd_llg_rhs": [_P, _P, _P, _P],
+    "gbd_llg_step": [_P, _P, _I, _D, _P],
+    "gbd_mesh_destroy": [_P],
+    "gbd_tensor_at": [ctypes.POINTER(gbd_mesh_desc), _I, _I, _I, ctypes.POINTER(_D)],
+    "gbd_plan_dims": [ctypes.POINTER(gbd_mesh_desc), ctypes.POINTER(_I)],
+    "gbd_kernel_spectrum_host": [ctypes.POINTER(gbd_mesh_desc), ctypes.POINTER(_D), ctypes.c_size_t],
+    "gbd_mesh_set_timing": [_P, _I],
+    "gbd_mesh_read_timing": [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)],
+}
+PASS_NAMES = ["row_fwd", "row_inv", "row_rk", "film_conv", "y_fwd", "z_conv", "y_inv", "unused"]
+GBD_NPASS = 8
+
+
+def load():
+    """Loads the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libgbdemag.so is not built: run `python -m paper_2308_08447_gb300.build` "
+                          "(or __graft_entry__.build()); there is no fallback path")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, args in _SIG.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.gbd_last_error.argtypes = []
+    lib.gbd_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def header_symbols():
+    """Function names declared in include/gbdemag.h."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"\b(gbd_[a-z_0-9]+)\s*\(", text)))
+
+
+def _check(status):
+    if status != GBD_OK:
+        raise GbdError(status, load().gbd_last_error().decode())
+
+
+def make_desc(n, cell, Ms, A_ex=0.0, alpha=0.0, gamma=0.0, Hext=(0.0, 0.0, 0.0), precision=GBD_FP32):
+    d = gbd_mesh_desc()
+    d.nx, d.ny, d.nz = (int(v) for v in n)
+    d.dx, d.dy, d.dz = (float(v) for v in cell)
+    d.Ms, d.A_ex, d.alpha, d.gamma = float(Ms), float(A_ex), float(alpha), float(gamma)
+    d.Hext[0], d.Hext[1], d.Hext[2] = (float(v) for v in Hext)
+    d.precision = int(precision)
+    d.flags = 0
+    return d
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _field_ptr(t, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous float32 CUDA tensor" % name)
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---- the C ABI, one Python function per entry point -----------------------------------------
+
+def gbd_mesh_create(desc):
+    h = ctypes.c_void_p()
+    _check(load().gbd_mesh_create(ctypes.byref(desc), ctypes.byref(h)))
+    return h
+
+
+def gbd_mesh_bytes(desc):
+    out = ctypes.c_size_t()
+    _check(load().gbd_mesh_bytes(ctypes.byref(desc), ctypes.byref(out)))
+    return out.value
+
+
+def gbd_set_kernel(mesh, stream=None):
+    _check(load().gbd_set_kernel(mesh, _stream_ptr(stream)))
+
+
+def gbd_demag(mesh, M, H, shape, stream=None):
+    _check(load().gbd_demag(mesh, _field_ptr(M, shape, "M"), _field_ptr(H, shape, "H"), _stream_ptr(stream)))
+
+
+def gbd_effective_field(mesh, m, H, shape, stream=None):
+    _check(load().gbd_effective_field(mesh, _field_ptr(m, shape, "m"), _field_ptr(H, shape, "H"),
+                                      _stream_ptr(stream)))
+
+
+def gbd_llg_rhs(mesh, m, dmdt, shape, stream=None):
+    _check(load().gbd_llg_rhs(mesh, _field_ptr(m, shape, "m"), _field_ptr(dmdt, shape, "dmdt"),
+                              _stream_ptr(stream)))
+
+
+def gbd_llg_step(mesh, m, nsteps, dt, shape, stream=None):
+    _check(load().gbd_llg_step(mesh, _field_ptr(m, shape, "m"), int(nsteps), float(dt), _stream_ptr(stream)))
+
+
+def gbd_mesh_destroy(mesh):
+    _check(load().gbd_mesh_destroy(mesh))
+
+
+def gbd_mesh_set_timing(mesh, enable):
+    _check(load().gbd_mesh_set_timing(mesh, 1 if enable else 0))
+
+
+def gbd_mesh_read_timing(mesh):
+    """{pass name: (total ms, launches)} since the last read."""
+    ms = (ctypes.c_double * GBD_NPASS)()
+    n = (ctypes.c_longlong * GBD_NPASS)()
+    _check(load().gbd_mesh_read_timing(mesh, ms, n))
+    return {PASS_NAMES[i]: (ms[i], n[i]) for i in range(GBD_NPASS) if n[i]}
+
+
+def gbd_last_error():
+    return load().gbd_last_error().decode()
+
+
+def gbd_tensor_at(desc, X, Y, Z):
+    out = (ctypes.c_double * 6)()
+    _check(load().gbd_tensor_at(ctypes.byref(desc), int(X), int(Y), int(Z), out))
+    return list(out)
+
+
+def gbd_plan_dims(desc):
+    out = (ctypes.c_int * 6)()
+    _check(load().gbd_plan_dims(ctypes.byref(desc), out))
+    return tuple(out)
+
+
+def gbd_kernel_spectrum_host(desc):
+    import numpy as np
+    Px, Py, Pz, Hx, Ky, Kz = gbd_plan_dims(desc)
+    out = np.zeros((6, Kz, Ky, Hx), dtype=np.float64)
+    _check(load().gbd_kernel_spectrum_host(ctypes.byref(desc), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           out.size))
+    return out
+
+
+# ---- convenience wrapper --------------------------------------------------------------------
+
+class Mesh:
+    """One mesh: owns the library handle; the kernel spectrum is computed on construction."""
+
+    def __init__(self, n, cell, Ms, A_ex=0.0, alpha=0.0, gamma=0.0, Hext=(0.0, 0.0, 0.0),
+                 precision=GBD_FP32, set_kernel=True, stream=None):
+        self.n = tuple(int(v) for v in n)
+        self.shape = (3, self.n[2], self.n[1], self.n[0])
+        self.desc = make_desc(n, cell, Ms, A_ex, alpha, gamma, Hext, precision)
+        self.handle = gbd_mesh_create(self.desc)
+        if set_kernel:
+            gbd_set_kernel(self.handle, stream)
+
+    def demag(self, M, H, stream=None):
+        gbd_demag(self.handle, M, H, self.shape, stream)
+
+    def effective_field(self, m, H, stream=None):
+        gbd_effective_field(self.handle, m, H, self.shape, stream)
+
+    def llg_rhs(self, m, dmdt, stream=None):
+        gbd_llg_rhs(self.handle, m, dmdt, self.shape, stream)
+
+    def llg_step(self, m, nsteps, dt, stream=None):
+        gbd_llg_step(self.handle, m, nsteps, dt, self.shape, stream)
+
+    def close(self):
+        if self.handle is not None:
+            gbd_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
