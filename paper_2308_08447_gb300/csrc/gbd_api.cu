@@ -100,23 +100,11 @@ bool make_plan(int nx, int ny, int nz, Plan& p, const char** why) {
   p.Ky = p.Py / 2 + 1;
   p.Kz = p.Pz / 2 + 1;
   p.film = (nz == 1);
-  const long long rows = (long long)ny * nz;
-  // x rows: about 6144 complex values per block, RB * Lx a multiple of 16.
-  int RB = p.Lx >= 2048 ? 1 : 2048 / p.Lx;
-  while (RB > 1 && RB / 2 >= rows && RB * p.Lx / 2 >= 16) RB /= 2;
-  if (RB * p.Lx < 16) RB = 16 / p.Lx;
-  p.RB = RB;
-  int Cf = p.Py >= 2048 ? 1 : 2048 / p.Py;
-  while (Cf > 1 && Cf / 2 >= p.Hx && Cf * p.Py / 2 >= 16) Cf /= 2;
-  if (Cf * p.Py < 16) Cf = 16 / p.Py;
-  p.Cf = Cf;
-  int Cy = p.Py >= 4096 ? 1 : 4096 / p.Py;
-  p.Cy = Cy;
-  int Wz = p.Pz >= 2048 ? 1 : 2048 / p.Pz;
-  const long long Q = (long long)p.Hx * (ny > 1 ? p.Py : 1);
-  while (Wz > 1 && Wz / 2 >= Q && Wz * p.Pz / 2 >= 16) Wz /= 2;
-  if (Wz * p.Pz < 16) Wz = 16 / p.Pz;
-  p.Wz = Wz;
+  // block shapes (the kernels are compiled for these per transform length)
+  p.RB = row_rb(p.Lx);
+  p.Cf = film_cols(p.Py);
+  p.Cy = ypass_lines(p.Py);
+  p.Wz = zconv_cols(p.Pz);
   p.bytes_S = (size_t)3 * nz * p.Hx * ny * sizeof(float2);
   p.bytes_T = (!p.film && ny > 1) ? (size_t)3 * nz * p.Hx * p.Py * sizeof(float2) : 0;
   p.bytes_K = p.film ? (size_t)p.Hx * p.Ky * sizeof(float4) : (size_t)p.Hx * p.Ky * p.Kz * 6 * sizeof(float);
@@ -178,13 +166,9 @@ static gbd::RowArgs row_args(const gbd_mesh* m) {
   gbd::RowArgs a;
   std::memset(&a, 0, sizeof(a));
   a.nx = p.nx;
-  a.Lx = p.Lx;
-  a.Hx = p.Hx;
   a.ny = p.ny;
   a.nz = p.nz;
   a.rows = p.ny * p.nz;
-  a.RB = p.RB;
-  a.tw_stride = GBD_TW_LEN / p.Px;
   a.N = p.N;
   a.S = m->S;
   const double mu0 = 4.0e-7 * 3.14159265358979323846;
@@ -219,7 +203,6 @@ static void enqueue_conv(gbd_mesh* m, cudaStream_t st) {
   const gbd::Plan& p = m->p;
   gbd::ColArgs a = col_args(m);
   if (p.film) {
-    a.C = p.Cf;
     a.dst = m->S;
     a.Kf = static_cast<const float4*>(m->K);
     timed(m, GBD_PASS_FILM_CONV, st, [&] { gbd::launch_film_conv(a, m->tw, st); });
@@ -227,22 +210,18 @@ static void enqueue_conv(gbd_mesh* m, cudaStream_t st) {
   }
   a.K3 = static_cast<const float*>(m->K);
   if (p.ny > 1) {
-    a.lines_total = 3 * p.nz * p.Hx;
-    a.C = p.Cy;
+    a.lines_total = 3LL * p.nz * p.Hx;
     a.src = m->S;
     a.dst = m->T;
     timed(m, GBD_PASS_Y_FWD, st, [&] { gbd::launch_y_fwd(a, m->tw, st); });
-    a.C = p.Wz;
     a.dst = m->T;
     a.Q = (long long)p.Hx * p.Py;
     a.Pyq = p.Py;
     timed(m, GBD_PASS_Z_CONV, st, [&] { gbd::launch_z_conv(a, m->tw, st); });
-    a.C = p.Cy;
     a.src = m->T;
     a.dst = m->S;
     timed(m, GBD_PASS_Y_INV, st, [&] { gbd::launch_y_inv(a, m->tw, st); });
   } else {
-    a.C = p.Wz;
     a.dst = m->S;
     a.Q = p.Hx;
     a.Pyq = 1;
@@ -438,11 +417,15 @@ gbd_status gbd_demag(gbd_mesh* m, const float* M, float* H, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   gbd::RowArgs a = row_args(m);
   a.in = M;
-  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(gbd::ROW_FWD, true, a, m->tw, st); });
+  a.mode = gbd::ROW_FWD;
+  a.fwd_after = 1;
+  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, a, m->tw, st); });
   enqueue_conv(m, st);
   a.hscale = 1.f;
   a.out = H;
-  timed(m, GBD_PASS_ROW_INV, st, [&] { gbd::launch_row(gbd::ROW_H, false, a, m->tw, st); });
+  a.mode = gbd::ROW_H;
+  a.fwd_after = 0;
+  timed(m, GBD_PASS_ROW_INV, st, [&] { gbd::launch_row(m->p.Lx, a, m->tw, st); });
   return after_launch("gbd_demag");
 }
 
@@ -453,11 +436,15 @@ static gbd_status field_like(gbd_mesh* m, const float* mm, float* out, int mode,
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   gbd::RowArgs a = row_args(m);
   a.in = mm;
-  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(gbd::ROW_FWD, true, a, m->tw, st); });
+  a.mode = gbd::ROW_FWD;
+  a.fwd_after = 1;
+  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, a, m->tw, st); });
   enqueue_conv(m, st);
   a.ms = mm;
   a.out = out;
-  timed(m, GBD_PASS_ROW_INV, st, [&] { gbd::launch_row(mode, false, a, m->tw, st); });
+  a.mode = mode;
+  a.fwd_after = 0;
+  timed(m, GBD_PASS_ROW_INV, st, [&] { gbd::launch_row(m->p.Lx, a, m->tw, st); });
   return after_launch(name);
 }
 
@@ -480,7 +467,9 @@ gbd_status gbd_llg_step(gbd_mesh* m, float* mm, int nsteps, double dt, void* str
   gbd::RowArgs a = row_args(m);
   a.dt = (float)dt;
   a.in = mm;
-  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(gbd::ROW_FWD, true, a, m->tw, st); });
+  a.mode = gbd::ROW_FWD;
+  a.fwd_after = 1;
+  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, a, m->tw, st); });
   a.m0 = mm;
   a.m0_out = mm;
   a.acc = m->acc;
@@ -493,8 +482,9 @@ gbd_status gbd_llg_step(gbd_mesh* m, float* mm, int nsteps, double dt, void* str
       enqueue_conv(m, st);
       a.ms = ms[stage];
       a.mnext = mn[stage];
-      const bool fwd = !(last && stage == 3);
-      timed(m, GBD_PASS_ROW_RK, st, [&] { gbd::launch_row(gbd::ROW_RK1 + stage, fwd, a, m->tw, st); });
+      a.mode = gbd::ROW_RK1 + stage;
+      a.fwd_after = (last && stage == 3) ? 0 : 1;
+      timed(m, GBD_PASS_ROW_RK, st, [&] { gbd::launch_row(m->p.Lx, a, m->tw, st); });
     }
   }
   return after_launch("gbd_llg_step");

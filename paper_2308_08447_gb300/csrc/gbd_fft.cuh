@@ -1,24 +1,30 @@
 // Shared-memory Stockham FFT building blocks for the demag convolution passes.
 //
-// The convolution theorem step of Sec. II (Eq. 1 evaluated as FFT -> pointwise
-// product -> inverse FFT) needs length-L complex FFTs, L a power of two, along
-// x (half-length transform inside the real-to-complex step), y and z. Each
-// thread block holds `lines` lines of length L in shared memory, laid out
-// line-major with line stride LS (L plus optional padding). Every thread owns
-// E = 16 complex values per pass and runs E/R radix-R butterflies on them, so
-// a block has lines * L / 16 threads.
+// The convolution-theorem evaluation of Eq. 1 (Sec. II: FFT -> pointwise product ->
+// inverse FFT) needs length-L complex FFTs, L a power of two known at compile time, along
+// x (half-length transform inside the real-to-complex step), y and z. A thread block holds
+// LINES lines of length L; every thread owns 16 complex values per pass and runs 16/R
+// radix-R butterflies on them, so a block has LINES * L / 16 threads.
 //
-// Stockham autosort pass (radix R, Ns = product of the radices already done):
+// Forward Stockham pass P_s (radix R, Ns = product of the radices already applied):
 //   for butterfly j in [0, L/R):   k = j mod Ns
-//     v[r] = a[j + r L/R] * w^(r k),  w = exp(s 2 pi i / (Ns R))
-//     v    = DFT_R(v)
-//     a'[(j / Ns) Ns R + k + q Ns] = v[q]
-// After the last pass the line holds the DFT in natural order. s = -1 is the
-// forward transform, s = +1 the unnormalised inverse.
+//     v[r] = a[j + r L/R] * w^(r k),  w = exp(S 2 pi i / (Ns R))
+//     v    = DFT_R(v)                (sign S)
+//     a'[(j - k) R + k + q Ns] = v[q]
+// P_p ... P_1 is the DFT in natural order. Its adjoint P_1^H ... P_p^H, where P_s^H
+// reads at the positions P_s writes, applies the conjugate DFT_R and then the conjugate
+// twiddles, and writes at the positions P_s reads, is the unnormalised inverse DFT.
+// The convolution kernels run the forward chain, the kernel product and the adjoint
+// chain, so the last forward pass and the first adjoint pass touch the same positions
+// and fuse in registers with the product. In both chains the outer passes address the
+// data in natural order (j + r L/R), so they can read or write global memory directly.
 //
-// Twiddles come from one table tw[m] = exp(-2 pi i m / GBD_TW_LEN) written on
-// the host in FP64 and rounded to FP32; a length-L transform reads it with
-// stride GBD_TW_LEN / (Ns R).
+// Shared memory rows are padded: element i of a line sits at i + i/16, which makes the
+// stride-16 accesses of the Ns = 1 pass and its adjoint conflict free.
+//
+// Twiddles come from one table tw[m] = exp(-2 pi i m / GBD_TW_LEN) written on the host
+// in FP64 and rounded to FP32. A butterfly loads w, w^2, w^4, w^8 and forms the other
+// powers with at most three complex products.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -34,27 +40,52 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
-// multiply by i (s = +1) or -i (s = -1)
 template <int S>
-__device__ __forceinline__ float2 cmul_i(float2 a) {
+__device__ __forceinline__ float2 cmul_i(float2 a) {  // a * (S i)
   return S > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
-// exp(S * 2 pi i * m / GBD_TW_LEN) from the table (S = -1 table value, +1 its conjugate).
+// exp(S 2 pi i m / GBD_TW_LEN)
 template <int S>
 __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int m) {
   float2 w = __ldg(tw + (m & (GBD_TW_LEN - 1)));
   return S < 0 ? w : cconj(w);
 }
 
-// ---- register DFTs of size 2, 4, 8, 16 (sign S) -------------------------------------------
-template <int S>
-__device__ __forceinline__ void dft2(float2& a, float2& b) {
-  float2 t = a;
-  a = cadd(t, b);
-  b = csub(t, b);
+// ---- radix decomposition (compile time) -------------------------------------------------
+__host__ __device__ constexpr int ilog2(int L) { return L <= 1 ? 0 : 1 + ilog2(L / 2); }
+
+// Passes of radix 16 and one remainder. With CONV the last radix is at most 8 (the
+// convolution kernels keep three components of that pass in registers).
+__host__ __device__ constexpr int npasses(int L, bool conv) {
+  return ilog2(L) == 0 ? 0
+         : ilog2(L) % 4 == 0 ? (conv ? ilog2(L) / 4 + 1 : ilog2(L) / 4)
+         : ilog2(L) % 4 == 3 ? ilog2(L) / 4 + 1
+         : (ilog2(L) <= 2 ? 1 : ilog2(L) / 4 + 1);
+}
+__host__ __device__ constexpr int radix_at(int L, bool conv, int p) {
+  // sequence: 16 ... 16, then the tail
+  return ilog2(L) % 4 == 0
+             ? (conv ? (p < ilog2(L) / 4 - 1 ? 16 : (p == ilog2(L) / 4 - 1 ? 2 : 8)) : 16)
+         : ilog2(L) % 4 == 3 ? (p < ilog2(L) / 4 ? 16 : 8)
+         : ilog2(L) == 1 ? 2
+         : ilog2(L) == 2 ? 4
+         : ilog2(L) % 4 == 1 ? (p < (ilog2(L) - 5) / 4 ? 16 : (p == (ilog2(L) - 5) / 4 ? 4 : 8))
+                             : (p < (ilog2(L) - 6) / 4 ? 16 : 8);
+}
+__host__ __device__ constexpr int ns_at(int L, bool conv, int p) {
+  return p == 0 ? 1 : ns_at(L, conv, p - 1) * radix_at(L, conv, p - 1);
 }
 
+// padded position of element i inside a shared-memory line
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+// float2 slots per line; LF (lines interleaved across threads) needs an odd stride
+template <int L, bool LF>
+__host__ __device__ constexpr int line_stride() {
+  return (L + L / 16) + (LF ? ((L + L / 16) % 2 == 0 ? 1 : 0) : 0);
+}
+
+// ---- register DFTs of size 2, 4, 8, 16 (sign S) -----------------------------------------
 template <int S>
 __device__ __forceinline__ void dft4(float2* x) {
   float2 a0 = cadd(x[0], x[2]), a1 = csub(x[0], x[2]);
@@ -73,8 +104,8 @@ __device__ __forceinline__ void dft8(float2* x) {
   float2 o[4] = {x[1], x[3], x[5], x[7]};
   dft4<S>(e);
   dft4<S>(o);
-  float2 t1 = make_float2(h * (o[1].x - S * o[1].y), h * (o[1].y + S * o[1].x));  // w8^1 = h (1 + S i)
-  float2 t2 = cmul_i<S>(o[2]);                                                    // w8^2 = S i
+  float2 t1 = make_float2(h * (o[1].x - S * o[1].y), h * (o[1].y + S * o[1].x));   // w8^1 = h (1 + S i)
+  float2 t2 = cmul_i<S>(o[2]);                                                     // w8^2 = S i
   float2 t3 = make_float2(h * (-o[3].x - S * o[3].y), h * (-o[3].y + S * o[3].x)); // w8^3 = h (-1 + S i)
   x[0] = cadd(e[0], o[0]);
   x[4] = csub(e[0], o[0]);
@@ -88,7 +119,7 @@ __device__ __forceinline__ void dft8(float2* x) {
 
 template <int S>
 __device__ __forceinline__ void dft16(float2* x) {
-  // cos(q pi / 8), sin(q pi / 8) for q = 0..7
+  // cos(q pi / 8), sin(q pi / 8), q = 0..7
   const float c[8] = {1.0f, 0.92387953251128675613f, 0.70710678118654752440f, 0.38268343236508977173f,
                       0.0f, -0.38268343236508977173f, -0.70710678118654752440f, -0.92387953251128675613f};
   const float s[8] = {0.0f, 0.38268343236508977173f, 0.70710678118654752440f, 0.92387953251128675613f,
@@ -103,8 +134,7 @@ __device__ __forceinline__ void dft16(float2* x) {
   dft8<S>(o);
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    float2 w = make_float2(c[q], S * s[q]);
-    float2 t = cmul(o[q], w);
+    float2 t = (q == 0) ? o[0] : cmul(o[q], make_float2(c[q], S * s[q]));
     x[q] = cadd(e[q], t);
     x[q + 8] = csub(e[q], t);
   }
@@ -113,7 +143,9 @@ __device__ __forceinline__ void dft16(float2* x) {
 template <int R, int S>
 __device__ __forceinline__ void dft(float2* x) {
   if constexpr (R == 2) {
-    dft2<S>(x[0], x[1]);
+    float2 t = x[0];
+    x[0] = cadd(t, x[1]);
+    x[1] = csub(t, x[1]);
   } else if constexpr (R == 4) {
     dft4<S>(x);
   } else if constexpr (R == 8) {
@@ -123,89 +155,119 @@ __device__ __forceinline__ void dft(float2* x) {
   }
 }
 
-// ---- one Stockham pass over the lines of a block -------------------------------------------
-// Butterfly b in [0, lines * L / R) maps to (line, j): LINE_FAST puts consecutive b on
-// consecutive lines (for line-interleaved global data), otherwise on consecutive j.
-// LD(line, idx) -> float2 and ST(line, idx, v) do the memory traffic; when both touch
-// the same shared buffer the pass is in place, separated by the barrier between them.
-template <int R, int S, bool LINE_FAST, class LD, class ST>
-__device__ __forceinline__ void stockham_pass(int L, int Ns, int lines, const float2* __restrict__ tw,
-                                              LD ld, ST st) {
-  constexpr int NB = GBD_E / R;  // butterflies per thread
-  const int LR = L / R;
-  const int nthreads = blockDim.x;
+// w[r] = exp(S 2 pi i r k / (Ns R)), r in [0, R), from loads of w^1, w^2, w^4, w^8.
+template <int S, int R, int Ns>
+__device__ __forceinline__ void twiddles(const float2* __restrict__ tw, int k, float2* w) {
+  constexpr int step = GBD_TW_LEN / (Ns * R);
+  const int m = k * step;
+  w[0] = make_float2(1.f, 0.f);
+  w[1] = twiddle<S>(tw, m);
+  if constexpr (R >= 4) {
+    w[2] = twiddle<S>(tw, 2 * m);
+    w[3] = cmul(w[1], w[2]);
+  }
+  if constexpr (R >= 8) {
+    w[4] = twiddle<S>(tw, 4 * m);
+    w[5] = cmul(w[1], w[4]);
+    w[6] = cmul(w[2], w[4]);
+    w[7] = cmul(w[3], w[4]);
+  }
+  if constexpr (R >= 16) {
+    w[8] = twiddle<S>(tw, 8 * m);
+#pragma unroll
+    for (int r = 1; r < 8; ++r) w[8 + r] = cmul(w[r], w[8]);
+  }
+}
+
+// Forward butterfly: twiddle, then DFT. Adjoint butterfly: DFT, then twiddle.
+template <int S, int R, int Ns, bool ADJ>
+__device__ __forceinline__ void butterfly(float2* v, int k, const float2* __restrict__ tw) {
+  if constexpr (!ADJ) {
+    if constexpr (Ns > 1) {
+      float2 w[R];
+      twiddles<S, R, Ns>(tw, k, w);
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r]);
+    }
+    dft<R, S>(v);
+  } else {
+    dft<R, S>(v);
+    if constexpr (Ns > 1) {
+      float2 w[R];
+      twiddles<S, R, Ns>(tw, k, w);
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r]);
+    }
+  }
+}
+
+// One pass over LINES lines, block of exactly LINES * L / 16 threads. Butterfly b maps to
+// (line, j): LF puts consecutive b on consecutive lines, otherwise on consecutive j.
+// Forward: loads at j + r L/R, stores at (j-k) R + k + q Ns. Adjoint: the reverse.
+// LD(line, pos) -> float2, ST(line, pos, v). SYNC_MID separates loads from stores when the
+// pass works in place.
+template <int S, bool ADJ, int L, int R, int Ns, int LINES, bool LF, bool SYNC_MID, class LD, class ST>
+__device__ __forceinline__ void stockham_pass(const float2* __restrict__ tw, LD ld, ST st) {
+  constexpr int LR = L / R;
+  constexpr int NB = GBD_E / R;
+  constexpr int T = LINES * L / GBD_E;
   float2 v[NB][R];
   int bl[NB], bj[NB];
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
-    int b = threadIdx.x + i * nthreads;
+    const int b = threadIdx.x + i * T;
     int line, j;
-    if (LINE_FAST) {
-      line = b % lines;
-      j = b / lines;
+    if (LF) {
+      line = b % LINES;
+      j = b / LINES;
     } else {
       line = b / LR;
-      j = b - line * LR;
+      j = b % LR;
     }
     bl[i] = line;
     bj[i] = j;
+    const int k = j % Ns;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[i][r] = ld(line, j + r * LR);
+    for (int r = 0; r < R; ++r) v[i][r] = ld(line, ADJ ? (j - k) * R + k + r * Ns : j + r * LR);
   }
-  __syncthreads();
-  const int tstride = GBD_TW_LEN / (Ns * R);
+  if (SYNC_MID) __syncthreads();
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
     const int j = bj[i];
-    const int k = j & (Ns - 1);
-    if (Ns > 1) {
+    const int k = j % Ns;
+    butterfly<S, R, Ns, ADJ>(v[i], k, tw);
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[i][r] = cmul(v[i][r], twiddle<S>(tw, r * k * tstride));
-    }
-    dft<R, S>(v[i]);
-    const int base = (j - k) * R + k;
-#pragma unroll
-    for (int q = 0; q < R; ++q) st(bl[i], base + q * Ns, v[i][q]);
+    for (int q = 0; q < R; ++q) st(bl[i], ADJ ? j + q * LR : (j - k) * R + k + q * Ns, v[i][q]);
   }
-  __syncthreads();
 }
 
-// Radix of pass p for a length-L transform: 16s first, then the remainder 8, 4 or 2.
-__host__ __device__ inline int radix_count(int L) {
-  int n = 0;
-  while (L > 1) {
-    L = (L >= 16) ? L / 16 : 1;
-    ++n;
+// Passes [P0, P1) of the forward chain (sign S) in place in shared memory.
+template <int S, int L, bool CONV, int LINES, bool LF, int P, int PEND>
+__device__ __forceinline__ void fwd_passes_smem(float2* sm, const float2* __restrict__ tw) {
+  if constexpr (P < PEND) {
+    constexpr int R = radix_at(L, CONV, P);
+    constexpr int Ns = ns_at(L, CONV, P);
+    constexpr int LS = line_stride<L, LF>();
+    auto ld = [&](int line, int i) { return sm[line * LS + pad(i)]; };
+    auto st = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
+    stockham_pass<S, false, L, R, Ns, LINES, LF, true>(tw, ld, st);
+    __syncthreads();
+    fwd_passes_smem<S, L, CONV, LINES, LF, P + 1, PEND>(sm, tw);
   }
-  return n;
 }
 
-// Full length-L transform of every line in place in shared memory.
-// buf: line-major, line stride LS (float2 units).
-template <int S, bool LINE_FAST>
-__device__ void fft_lines_smem(float2* buf, int L, int LS, int lines, const float2* __restrict__ tw) {
-  auto ld = [=](int line, int idx) { return buf[line * LS + idx]; };
-  auto st = [=](int line, int idx, float2 v) { buf[line * LS + idx] = v; };
-  int Ns = 1;
-  int rem = L;
-  while (rem > 1) {
-    if (rem >= 16) {
-      stockham_pass<16, S, LINE_FAST>(L, Ns, lines, tw, ld, st);
-      Ns *= 16;
-      rem /= 16;
-    } else if (rem == 8) {
-      stockham_pass<8, S, LINE_FAST>(L, Ns, lines, tw, ld, st);
-      Ns *= 8;
-      rem = 1;
-    } else if (rem == 4) {
-      stockham_pass<4, S, LINE_FAST>(L, Ns, lines, tw, ld, st);
-      Ns *= 4;
-      rem = 1;
-    } else {
-      stockham_pass<2, S, LINE_FAST>(L, Ns, lines, tw, ld, st);
-      Ns *= 2;
-      rem = 1;
-    }
+// Adjoint passes P-1 down to PEND (inclusive) in place in shared memory.
+template <int S, int L, bool CONV, int LINES, bool LF, int P, int PEND>
+__device__ __forceinline__ void adj_passes_smem(float2* sm, const float2* __restrict__ tw) {
+  if constexpr (P > PEND) {
+    constexpr int R = radix_at(L, CONV, P - 1);
+    constexpr int Ns = ns_at(L, CONV, P - 1);
+    constexpr int LS = line_stride<L, LF>();
+    auto ld = [&](int line, int i) { return sm[line * LS + pad(i)]; };
+    auto st = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
+    stockham_pass<S, true, L, R, Ns, LINES, LF, true>(tw, ld, st);
+    __syncthreads();
+    adj_passes_smem<S, L, CONV, LINES, LF, P - 1, PEND>(sm, tw);
   }
 }
 

@@ -9,229 +9,219 @@
 //   row kernel, inverse:  x complex-to-real + crop, then the mode's epilogue; the RK4
 //                         modes also run the next stage's forward x transform.
 // The padding is never stored: loads past n_d read zeros and cropped outputs are not
-// written, so S keeps ny rows and T keeps nz planes.
+// written, so S keeps ny rows and T keeps nz planes. Every transform length is a
+// template parameter; the host dispatches on it.
 #include "gbd_fft.cuh"
 #include "gbd_kernels.cuh"
 
 namespace gbd {
 
+__host__ __device__ constexpr int min_blocks(int T) { return T >= 768 ? 1 : 768 / T; }
+
 // ---------------------------------------------------------------------------------------------
-// x rows: real-to-complex through a half-length complex FFT.
-// For a real row x of length Px = 2 Lx: z[m] = x[2m] + i x[2m+1], Z = FFT_Lx(z), then for
-// k in [0, Lx]:  X[k] = (Z[k] + Z*[Lx-k]) / 2 - (i/2) W^k (Z[k] - Z*[Lx-k]),  W = exp(-2 pi i / Px).
-// The inverse builds Z[k] = (X[k] + X*[Lx-k]) + i W^-k (X[k] - X*[Lx-k]) and its unnormalised
-// inverse FFT gives x[2m] + i x[2m+1] (times nothing: the 1/P factors live in the kernel).
+// x rows: real-to-complex through a half-length complex FFT (Lx = Px / 2).
+// Forward: z[m] = x[2m] + i x[2m+1], Z = FFT_Lx(z), and for k in [0, Lx]
+//   X[k] = (Z[k] + Z*[Lx-k]) / 2 - (i/2) W^k (Z[k] - Z*[Lx-k]),  W = exp(-2 pi i / Px).
+// Inverse: Z[k] = (X[k] + X*[Lx-k]) + i W^-k (X[k] - X*[Lx-k]); the unnormalised inverse
+// FFT of Z is x[2m] + i x[2m+1] (the 1/P factors are folded into the kernel spectrum).
+// Only the first Lx/2 complex values (the first Lx >= nx real samples) are produced by the
+// inverse, and the forward reads only those: the upper half is the zero padding.
 // ---------------------------------------------------------------------------------------------
 
-__device__ __forceinline__ long long s_index(int c, int z, int kx, int y, int nz, int Hx, int ny) {
-  return ((long long)(c * nz + z) * Hx + kx) * ny + y;
-}
-
-template <int MODE, bool FWD_AFTER>
-__global__ void __launch_bounds__(1024) row_kernel(RowArgs a, const float2* __restrict__ tw) {
+template <int LX>
+__global__ void __launch_bounds__(3 * row_rb(LX) * LX / GBD_E, min_blocks(3 * row_rb(LX) * LX / GBD_E))
+    row_kernel(RowArgs a, const float2* __restrict__ tw) {
+  constexpr int RB = row_rb(LX);
+  constexpr int LINES = 3 * RB;
+  constexpr int T = LINES * LX / GBD_E;
+  constexpr int LS = line_stride<LX, false>();
+  constexpr int NP = npasses(LX, false);
+  constexpr int HX = LX + 1;
+  constexpr int HALF = LX / 2;
+  constexpr int TWS = GBD_TW_LEN / (2 * LX);   // W_Px^k = tw[k * TWS]
+  constexpr int FL = NP >= 1 ? LX : 2 * LX;    // real samples the forward transform reads
   extern __shared__ float2 sm[];
-  const int LS = a.Lx + 1;          // line stride (float2); slot Lx holds X[Lx] while staging
-  const int RB = a.RB;
-  const int lines = 3 * RB;
   const int r0 = blockIdx.x * RB;
-  const int T = blockDim.x;
   const long long N = a.N;
+  const int mode = a.mode;
+  const int nx = a.nx, ny = a.ny;
 
-  if (MODE != ROW_FWD) {
-    // 1. stage the half spectrum X[kx], kx in [0, Hx), of the block's rows (rr fastest).
-    for (int e = threadIdx.x; e < lines * a.Hx; e += T) {
-      int rr = e % RB;
-      int t2 = e / RB;
-      int c = t2 % 3;
-      int kx = t2 / 3;
-      int row = r0 + rr;
-      float2 v = make_float2(0.f, 0.f);
+  if (mode != ROW_FWD) {
+    // 1. X (global, [kx][y] layout) -> Z pairwise into shared memory; rows fastest.
+    for (int e = threadIdx.x; e < RB * 3 * (HALF + 1); e += T) {
+      const int rr = e % RB;
+      const int t2 = e / RB;
+      const int c = t2 % 3;
+      const int k = t2 / 3;
+      const int row = r0 + rr;
+      float2 zk = make_float2(0.f, 0.f), zl = zk;
       if (row < a.rows) {
-        int z = row / a.ny, y = row - (row / a.ny) * a.ny;
-        v = a.S[s_index(c, z, kx, y, a.nz, a.Hx, a.ny)];
-      }
-      sm[(c * RB + rr) * LS + kx] = v;
-    }
-    __syncthreads();
-    // 2. X -> Z pairwise, (k, Lx - k) for k in [0, Lx/2].
-    const int half = a.Lx / 2;
-    for (int e = threadIdx.x; e < lines * (half + 1); e += T) {
-      int line = e / (half + 1);
-      int k = e - line * (half + 1);
-      float2* L = sm + line * LS;
-      if (k == 0) {
-        float2 A = L[0], B = L[a.Lx];
-        float2 s = cadd(A, cconj(B)), d = csub(A, cconj(B));
-        L[0] = cadd(s, cmul_i<1>(d));
-      } else {
-        float2 A = L[k], B = L[a.Lx - k];
-        float2 wm = twiddle<1>(tw, k * a.tw_stride);   // W^-k = exp(+2 pi i k / Px)
-        float2 wp = twiddle<-1>(tw, k * a.tw_stride);  // W^k
-        float2 zk = cadd(cadd(A, cconj(B)), cmul_i<1>(cmul(wm, csub(A, cconj(B)))));
-        float2 zl = csub(cadd(B, cconj(A)), cmul_i<1>(cmul(wp, csub(B, cconj(A)))));
-        L[k] = zk;
-        if (a.Lx - k != k) L[a.Lx - k] = zl;
-      }
-    }
-    __syncthreads();
-    // 3. unnormalised inverse FFT of length Lx on every line.
-    fft_lines_smem<1, false>(sm, a.Lx, LS, lines, tw);
-    // 4. epilogue on the real rows: float view xs[x] = x_un[x], x < nx.
-    for (int e = threadIdx.x; e < RB * a.nx; e += T) {
-      int rr = e / a.nx;
-      int x = e - rr * a.nx;
-      int row = r0 + rr;
-      if (row >= a.rows) continue;
-      const long long idx = (long long)row * a.nx + x;
-      float hd[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) hd[c] = reinterpret_cast<const float*>(sm + (c * RB + rr) * LS)[x] * a.hscale;
-      if (MODE == ROW_H) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) a.out[c * N + idx] = hd[c];
-        continue;
-      }
-      // exchange: 7-point Laplacian, free boundaries (missing neighbour = the cell itself)
-      const int z = row / a.ny, y = row - z * a.ny;
-      const long long sx = 1, sy = a.nx, sz = (long long)a.nx * a.ny;
-      const long long ixm = x > 0 ? idx - sx : idx, ixp = x < a.nx - 1 ? idx + sx : idx;
-      const long long iym = y > 0 ? idx - sy : idx, iyp = y < a.ny - 1 ? idx + sy : idx;
-      const long long izm = z > 0 ? idx - sz : idx, izp = z < a.nz - 1 ? idx + sz : idx;
-      float m[3], H[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float* p = a.ms + c * N;
-        float mc = p[idx];
-        m[c] = mc;
-        float lap = a.cx * (p[ixp] - 2.f * mc + p[ixm]) + a.cy * (p[iyp] - 2.f * mc + p[iym]) +
-                    a.cz * (p[izp] - 2.f * mc + p[izm]);
-        H[c] = hd[c] + lap;
-      }
-      H[0] += a.hx;
-      H[1] += a.hy;
-      H[2] += a.hz;
-      if (MODE == ROW_HEFF) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) a.out[c * N + idx] = H[c];
-        continue;
-      }
-      // dm/dt = -gamma/(1+alpha^2) [m x H + alpha m x (m x H)]
-      float mxH[3] = {m[1] * H[2] - m[2] * H[1], m[2] * H[0] - m[0] * H[2], m[0] * H[1] - m[1] * H[0]};
-      float mmH[3] = {m[1] * mxH[2] - m[2] * mxH[1], m[2] * mxH[0] - m[0] * mxH[2], m[0] * mxH[1] - m[1] * mxH[0]};
-      float f[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) f[c] = -a.geff * (mxH[c] + a.alpha * mmH[c]);
-      if (MODE == ROW_RHS) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) a.out[c * N + idx] = f[c];
-        continue;
-      }
-      float mn[3];
-      if (MODE == ROW_RK1) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          a.acc[c * N + idx] = f[c];
-          mn[c] = m[c] + 0.5f * a.dt * f[c];
-          a.mnext[c * N + idx] = mn[c];
-        }
-      } else if (MODE == ROW_RK2 || MODE == ROW_RK3) {
-        const float h = (MODE == ROW_RK2) ? 0.5f * a.dt : a.dt;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          a.acc[c * N + idx] += 2.f * f[c];
-          mn[c] = a.m0[c * N + idx] + h * f[c];
-          a.mnext[c * N + idx] = mn[c];
-        }
-      } else {  // ROW_RK4
-        const float h = a.dt * (1.0f / 6.0f);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) mn[c] = a.m0[c * N + idx] + h * (a.acc[c * N + idx] + f[c]);
-        float inv = rsqrtf(mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          mn[c] *= inv;
-          a.m0_out[c * N + idx] = mn[c];
+        const int z = row / ny, y = row - z * ny;
+        const float2* base = a.S + (long long)(c * a.nz + z) * HX * ny + y;
+        const float2 A = base[(long long)k * ny];
+        const float2 B = base[(long long)(LX - k) * ny];
+        if (k == 0) {
+          zk = cadd(cadd(A, cconj(B)), cmul_i<1>(csub(A, cconj(B))));
+        } else {
+          const float2 wp = twiddle<-1>(tw, k * TWS);  // W^k
+          const float2 wm = cconj(wp);                  // W^-k
+          zk = cadd(cadd(A, cconj(B)), cmul_i<1>(cmul(wm, csub(A, cconj(B)))));
+          zl = csub(cadd(B, cconj(A)), cmul_i<1>(cmul(wp, csub(B, cconj(A)))));
         }
       }
-      if (FWD_AFTER) {
+      float2* L = sm + (c * RB + rr) * LS;
+      L[pad(k)] = zk;
+      if (k != 0 && k != LX - k) L[pad(LX - k)] = zl;
+    }
+    __syncthreads();
+    // 2. unnormalised inverse FFT: adjoint passes, the last one keeping the lower half only.
+    if constexpr (NP >= 1) {
+      adj_passes_smem<1, LX, false, LINES, false, NP, 1>(sm, tw);
+      auto ld = [&](int line, int i) { return sm[line * LS + pad(i)]; };
+      auto st = [&](int line, int i, float2 v) {
+        if (i < HALF) sm[line * LS + pad(i)] = v;
+      };
+      stockham_pass<1, true, LX, radix_at(LX, false, 0), 1, LINES, false, true>(tw, ld, st);
+      __syncthreads();
+    }
+    // 3. epilogue on the real rows: float view of line position x is 2 pad(x/2) + (x & 1).
+    for (int rr = 0; rr < RB; ++rr) {
+      const int row = r0 + rr;
+      if (row >= a.rows) break;
+      const int z = row / ny, y = row - z * ny;
+      for (int x = threadIdx.x; x < nx; x += T) {
+        const long long idx = (long long)row * nx + x;
+        const int fpos = 2 * pad(x >> 1) + (x & 1);
+        float hd[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) reinterpret_cast<float*>(sm + (c * RB + rr) * LS)[x] = mn[c];
+        for (int c = 0; c < 3; ++c) hd[c] = reinterpret_cast<const float*>(sm + (c * RB + rr) * LS)[fpos] * a.hscale;
+        if (mode == ROW_H) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) a.out[c * N + idx] = hd[c];
+          continue;
+        }
+        // exchange: 7-point Laplacian, free boundaries (missing neighbour = the cell itself)
+        const long long sy = nx, sz = (long long)nx * ny;
+        const long long ixm = x > 0 ? idx - 1 : idx, ixp = x < nx - 1 ? idx + 1 : idx;
+        const long long iym = y > 0 ? idx - sy : idx, iyp = y < ny - 1 ? idx + sy : idx;
+        const long long izm = z > 0 ? idx - sz : idx, izp = z < a.nz - 1 ? idx + sz : idx;
+        float m[3], H[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float* p = a.ms + c * N;
+          const float mc = p[idx];
+          m[c] = mc;
+          const float lap = a.cx * (p[ixp] - 2.f * mc + p[ixm]) + a.cy * (p[iyp] - 2.f * mc + p[iym]) +
+                            a.cz * (p[izp] - 2.f * mc + p[izm]);
+          H[c] = hd[c] + lap;
+        }
+        H[0] += a.hx;
+        H[1] += a.hy;
+        H[2] += a.hz;
+        if (mode == ROW_HEFF) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) a.out[c * N + idx] = H[c];
+          continue;
+        }
+        // dm/dt = -gamma/(1+alpha^2) [m x H + alpha m x (m x H)]
+        const float mxH[3] = {m[1] * H[2] - m[2] * H[1], m[2] * H[0] - m[0] * H[2], m[0] * H[1] - m[1] * H[0]};
+        const float mmH[3] = {m[1] * mxH[2] - m[2] * mxH[1], m[2] * mxH[0] - m[0] * mxH[2],
+                              m[0] * mxH[1] - m[1] * mxH[0]};
+        float f[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) f[c] = -a.geff * (mxH[c] + a.alpha * mmH[c]);
+        if (mode == ROW_RHS) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) a.out[c * N + idx] = f[c];
+          continue;
+        }
+        float mn[3];
+        if (mode == ROW_RK1) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            a.acc[c * N + idx] = f[c];
+            mn[c] = m[c] + 0.5f * a.dt * f[c];
+            a.mnext[c * N + idx] = mn[c];
+          }
+        } else if (mode == ROW_RK2 || mode == ROW_RK3) {
+          const float h = (mode == ROW_RK2) ? 0.5f * a.dt : a.dt;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            a.acc[c * N + idx] += 2.f * f[c];
+            mn[c] = a.m0[c * N + idx] + h * f[c];
+            a.mnext[c * N + idx] = mn[c];
+          }
+        } else {  // ROW_RK4
+          const float h = a.dt * (1.0f / 6.0f);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) mn[c] = a.m0[c * N + idx] + h * (a.acc[c * N + idx] + f[c]);
+          const float inv = rsqrtf(mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            mn[c] *= inv;
+            a.m0_out[c * N + idx] = mn[c];
+          }
+        }
+        if (a.fwd_after) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) reinterpret_cast<float*>(sm + (c * RB + rr) * LS)[fpos] = mn[c];
+        }
       }
     }
-    if (!FWD_AFTER) return;
+    if (!a.fwd_after) return;  // uniform over the block
     __syncthreads();
-  }
-
-  // 5. forward: rows in the float view, zero from nx up to Px (= 2 Lx floats).
-  if (MODE == ROW_FWD) {
-    for (int e = threadIdx.x; e < lines * 2 * a.Lx; e += T) {
-      int line = e / (2 * a.Lx);
-      int x = e - line * 2 * a.Lx;
-      int c = line / RB, rr = line - c * RB;
-      int row = r0 + rr;
-      float v = 0.f;
-      if (x < a.nx && row < a.rows) v = a.in[c * N + (long long)row * a.nx + x];
-      reinterpret_cast<float*>(sm + line * LS)[x] = v;
+    // 4. zero what the forward transform reads beyond the data
+    for (int line = 0; line < LINES; ++line) {
+      const int rr = line % RB;
+      const int x0 = (r0 + rr < a.rows) ? nx : 0;
+      float* fl = reinterpret_cast<float*>(sm + line * LS);
+      for (int x = x0 + threadIdx.x; x < FL; x += T) fl[2 * pad(x >> 1) + (x & 1)] = 0.f;
     }
   } else {
-    for (int e = threadIdx.x; e < lines * 2 * a.Lx; e += T) {
-      int line = e / (2 * a.Lx);
-      int x = e - line * 2 * a.Lx;
-      int rr = line % RB;
-      if (x >= a.nx || r0 + rr >= a.rows) reinterpret_cast<float*>(sm + line * LS)[x] = 0.f;
+    // forward only: the input rows into the float view, zero beyond nx
+    for (int e = threadIdx.x; e < LINES * FL; e += T) {
+      const int line = e / FL;
+      const int x = e % FL;
+      const int c = line / RB, rr = line % RB;
+      const int row = r0 + rr;
+      float v = 0.f;
+      if (x < nx && row < a.rows) v = a.in[c * N + (long long)row * nx + x];
+      reinterpret_cast<float*>(sm + line * LS)[2 * pad(x >> 1) + (x & 1)] = v;
     }
   }
   __syncthreads();
-  fft_lines_smem<-1, false>(sm, a.Lx, LS, lines, tw);
-  // 6. Z -> X pairwise and store the half spectrum (rr fastest for the [kx][y] layout).
-  const int half = a.Lx / 2;
-  for (int e = threadIdx.x; e < lines * (half + 1); e += T) {
-    int rr = e % RB;
-    int t2 = e / RB;
-    int c = t2 % 3;
-    int k = t2 / 3;
-    int row = r0 + rr;
-    if (row >= a.rows) continue;
-    int z = row / a.ny, y = row - z * a.ny;
-    const float2* L = sm + (c * RB + rr) * LS;
-    if (k == 0) {
-      float2 A = L[0];
-      a.S[s_index(c, z, 0, y, a.nz, a.Hx, a.ny)] = make_float2(A.x + A.y, 0.f);
-      a.S[s_index(c, z, a.Lx, y, a.nz, a.Hx, a.ny)] = make_float2(A.x - A.y, 0.f);
-    } else {
-      float2 A = L[k], B = L[a.Lx - k];
-      float2 wp = twiddle<-1>(tw, k * a.tw_stride);  // W^k
-      float2 wm = twiddle<1>(tw, k * a.tw_stride);   // W^-k
-      float2 xk = csub(cadd(A, cconj(B)), cmul_i<1>(cmul(wp, csub(A, cconj(B)))));
-      float2 xl = cadd(cadd(B, cconj(A)), cmul_i<1>(cmul(wm, csub(B, cconj(A)))));
-      a.S[s_index(c, z, k, y, a.nz, a.Hx, a.ny)] = cscale(xk, 0.5f);
-      if (a.Lx - k != k) a.S[s_index(c, z, a.Lx - k, y, a.nz, a.Hx, a.ny)] = cscale(xl, 0.5f);
-    }
+  // 5. forward FFT; the first pass reads the lower half only (the upper half is zero).
+  if constexpr (NP >= 1) {
+    auto ld = [&](int line, int i) { return i < HALF ? sm[line * LS + pad(i)] : make_float2(0.f, 0.f); };
+    auto st = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
+    stockham_pass<-1, false, LX, radix_at(LX, false, 0), 1, LINES, false, true>(tw, ld, st);
+    __syncthreads();
+    fwd_passes_smem<-1, LX, false, LINES, false, 1, NP>(sm, tw);
   }
-}
-
-size_t row_smem_bytes(int RB, int Lx) { return (size_t)3 * RB * (Lx + 1) * sizeof(float2); }
-int row_threads(int RB, int Lx) { return 3 * RB * Lx / GBD_E; }
-
-template <int MODE, bool FWD>
-static void row_launch_t(const RowArgs& a, const float2* tw, cudaStream_t st) {
-  int blocks = (a.rows + a.RB - 1) / a.RB;
-  size_t smem = row_smem_bytes(a.RB, a.Lx);
-  auto k = row_kernel<MODE, FWD>;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k<<<blocks, row_threads(a.RB, a.Lx), smem, st>>>(a, tw);
-}
-
-void launch_row(int mode, bool fwd_after, const RowArgs& a, const float2* tw, cudaStream_t st) {
-  switch (mode) {
-    case ROW_FWD: row_launch_t<ROW_FWD, true>(a, tw, st); break;
-    case ROW_H: row_launch_t<ROW_H, false>(a, tw, st); break;
-    case ROW_HEFF: row_launch_t<ROW_HEFF, false>(a, tw, st); break;
-    case ROW_RHS: row_launch_t<ROW_RHS, false>(a, tw, st); break;
-    case ROW_RK1: fwd_after ? row_launch_t<ROW_RK1, true>(a, tw, st) : row_launch_t<ROW_RK1, false>(a, tw, st); break;
-    case ROW_RK2: fwd_after ? row_launch_t<ROW_RK2, true>(a, tw, st) : row_launch_t<ROW_RK2, false>(a, tw, st); break;
-    case ROW_RK3: fwd_after ? row_launch_t<ROW_RK3, true>(a, tw, st) : row_launch_t<ROW_RK3, false>(a, tw, st); break;
-    default: fwd_after ? row_launch_t<ROW_RK4, true>(a, tw, st) : row_launch_t<ROW_RK4, false>(a, tw, st); break;
+  // 6. Z -> X pairwise and store the half spectrum (rows fastest for the [kx][y] layout).
+  for (int e = threadIdx.x; e < RB * 3 * (HALF + 1); e += T) {
+    const int rr = e % RB;
+    const int t2 = e / RB;
+    const int c = t2 % 3;
+    const int k = t2 / 3;
+    const int row = r0 + rr;
+    if (row >= a.rows) continue;
+    const int z = row / ny, y = row - z * ny;
+    const float2* L = sm + (c * RB + rr) * LS;
+    float2* base = a.S + (long long)(c * a.nz + z) * HX * ny + y;
+    if (k == 0) {
+      const float2 A = L[pad(0)];
+      base[0] = make_float2(A.x + A.y, 0.f);
+      base[(long long)LX * ny] = make_float2(A.x - A.y, 0.f);
+    } else {
+      const float2 A = L[pad(k)], B = L[pad(LX - k)];
+      const float2 wp = twiddle<-1>(tw, k * TWS);  // W^k
+      const float2 wm = cconj(wp);
+      const float2 xk = csub(cadd(A, cconj(B)), cmul_i<1>(cmul(wp, csub(A, cconj(B)))));
+      const float2 xl = cadd(cadd(B, cconj(A)), cmul_i<1>(cmul(wm, csub(B, cconj(A)))));
+      base[(long long)k * ny] = cscale(xk, 0.5f);
+      if (LX - k != k) base[(long long)(LX - k) * ny] = cscale(xl, 0.5f);
+    }
   }
 }
 
@@ -239,170 +229,368 @@ void launch_row(int mode, bool fwd_after, const RowArgs& a, const float2* tw, cu
 // Kernel product H~_a = sum_b K~_ab M~_b with the packed real spectrum. Stored indices are
 // k' = k for k <= P/2 and P - k above; components odd along that axis change sign there
 // (xy, yz odd in y; xz, yz odd in z). The 1/(Px Py Pz) and the minus sign of Eq. 1 are in K~.
+// The last forward pass, the product and the first adjoint pass run in registers on one
+// thread per butterfly position j, for all three components.
 // ---------------------------------------------------------------------------------------------
 
-// film: one block = C columns kx, all three components, Py points each.
-__global__ void __launch_bounds__(1024) film_conv_kernel(ColArgs a, const float2* __restrict__ tw) {
+template <int L, int RL, int NSL, class LD, class ST, class MUL>
+__device__ __forceinline__ void fused_item(int line0, int lstride, int j, const float2* __restrict__ tw, LD ld, ST st,
+                                           MUL mul) {
+  constexpr int LR = L / RL;
+  float2 v[3][RL];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int r = 0; r < RL; ++r) v[c][r] = ld(line0 + c * lstride, j + r * LR);
+  if constexpr (RL > 1) {
+    float2 w[RL];
+    if constexpr (NSL > 1) twiddles<-1, RL, NSL>(tw, j, w);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if constexpr (NSL > 1) {
+#pragma unroll
+        for (int r = 1; r < RL; ++r) v[c][r] = cmul(v[c][r], w[r]);
+      }
+      dft<RL, -1>(v[c]);
+    }
+#pragma unroll
+    for (int q = 0; q < RL; ++q) mul(j + q * LR, v[0][q], v[1][q], v[2][q]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      dft<RL, 1>(v[c]);
+      if constexpr (NSL > 1) {
+#pragma unroll
+        for (int r = 1; r < RL; ++r) v[c][r] = cmul(v[c][r], cconj(w[r]));
+      }
+    }
+  } else {
+    mul(j, v[0][0], v[1][0], v[2][0]);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int r = 0; r < RL; ++r) st(line0 + c * lstride, j + r * LR, v[c][r]);
+}
+
+// film: one block = C columns kx, three components each, lines = c * C + cc.
+template <int L>
+__global__ void __launch_bounds__(3 * film_cols(L) * L / GBD_E, min_blocks(3 * film_cols(L) * L / GBD_E))
+    film_conv_kernel(ColArgs a, const float2* __restrict__ tw) {
+  constexpr int C = film_cols(L);
+  constexpr int LINES = 3 * C;
+  constexpr int T = LINES * L / GBD_E;
+  constexpr int LS = line_stride<L, false>();
+  constexpr int NP = npasses(L, true);
+  constexpr int RL = NP >= 1 ? radix_at(L, true, NP - 1) : 1;
+  constexpr int NSL = NP >= 1 ? ns_at(L, true, NP - 1) : 1;
+  constexpr int LR = L / RL;
+  constexpr int KY = L / 2 + 1;
   extern __shared__ float2 sm[];
-  const int C = a.C, Py = a.Py, LS = Py;
-  const int lines = 3 * C;
   const int kx0 = blockIdx.x * C;
-  const int T = blockDim.x;
+  const int ny = a.ny, Hx = a.Hx;
   float2* S = a.dst;
-  for (int e = threadIdx.x; e < lines * Py; e += T) {
-    int line = e / Py;
-    int y = e - line * Py;
-    int c = line / C, cc = line - c * C;
-    int kx = kx0 + cc;
-    float2 v = make_float2(0.f, 0.f);
-    if (y < a.ny && kx < a.Hx) v = S[s_index(c, 0, kx, y, 1, a.Hx, a.ny)];
-    sm[line * LS + y] = v;
-  }
-  __syncthreads();
-  fft_lines_smem<-1, false>(sm, Py, LS, lines, tw);
-  const int Ky = Py / 2 + 1;
-  for (int e = threadIdx.x; e < C * Py; e += T) {
-    int cc = e / Py;
-    int ky = e - cc * Py;
-    int kx = kx0 + cc;
-    if (kx >= a.Hx) continue;
-    int kyp = ky;
-    float sy = 1.f;
-    if (Py > 1 && ky > Py / 2) {
-      kyp = Py - ky;
-      sy = -1.f;
+
+  auto gptr = [&](int line) { return S + (long long)((line / C) * Hx + kx0 + line % C) * ny; };
+  auto gld = [&](int line, int y) {
+    return (y < ny && kx0 + line % C < Hx) ? gptr(line)[y] : make_float2(0.f, 0.f);
+  };
+  auto gst = [&](int line, int y, float2 v) {
+    if (y < ny && kx0 + line % C < Hx) gptr(line)[y] = v;
+  };
+  auto sld = [&](int line, int i) { return sm[line * LS + pad(i)]; };
+  auto sst = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
+
+  auto run_fused = [&](auto ld, auto st) {
+    for (int it = threadIdx.x; it < C * LR; it += T) {
+      const int cc = it / LR, j = it % LR;
+      const int kx = kx0 + cc;
+      auto mul = [&](int ky, float2& m0, float2& m1, float2& m2) {
+        if (kx >= Hx) return;
+        int kyp = ky;
+        float sy = 1.f;
+        if (L > 1 && ky > L / 2) {
+          kyp = L - ky;
+          sy = -1.f;
+        }
+        const float4 k4 = __ldg(a.Kf + (long long)kx * KY + kyp);
+        const float kxy = sy * k4.w;
+        const float2 h0 = make_float2(k4.x * m0.x + kxy * m1.x, k4.x * m0.y + kxy * m1.y);
+        const float2 h1 = make_float2(kxy * m0.x + k4.y * m1.x, kxy * m0.y + k4.y * m1.y);
+        m2 = make_float2(k4.z * m2.x, k4.z * m2.y);
+        m0 = h0;
+        m1 = h1;
+      };
+      fused_item<L, RL, NSL>(cc, C, j, tw, ld, st, mul);
     }
-    float4 k4 = __ldg(a.Kf + (long long)kx * Ky + kyp);
-    float kxy = sy * k4.w;
-    float2 m0 = sm[(0 * C + cc) * LS + ky], m1 = sm[(1 * C + cc) * LS + ky], m2 = sm[(2 * C + cc) * LS + ky];
-    sm[(0 * C + cc) * LS + ky] = make_float2(k4.x * m0.x + kxy * m1.x, k4.x * m0.y + kxy * m1.y);
-    sm[(1 * C + cc) * LS + ky] = make_float2(kxy * m0.x + k4.y * m1.x, kxy * m0.y + k4.y * m1.y);
-    sm[(2 * C + cc) * LS + ky] = make_float2(k4.z * m2.x, k4.z * m2.y);
-  }
-  __syncthreads();
-  fft_lines_smem<1, false>(sm, Py, LS, lines, tw);
-  for (int e = threadIdx.x; e < lines * a.ny; e += T) {
-    int line = e / a.ny;
-    int y = e - line * a.ny;
-    int c = line / C, cc = line - c * C;
-    int kx = kx0 + cc;
-    if (kx < a.Hx) S[s_index(c, 0, kx, y, 1, a.Hx, a.ny)] = sm[line * LS + y];
+  };
+
+  if constexpr (NP <= 1) {
+    run_fused(gld, gst);
+  } else {
+    stockham_pass<-1, false, L, radix_at(L, true, 0), 1, LINES, false, false>(tw, gld, sst);
+    __syncthreads();
+    fwd_passes_smem<-1, L, true, LINES, false, 1, NP - 1>(sm, tw);
+    run_fused(sld, sst);
+    __syncthreads();
+    adj_passes_smem<1, L, true, LINES, false, NP - 1, 1>(sm, tw);
+    stockham_pass<1, true, L, radix_at(L, true, 0), 1, LINES, false, false>(tw, sld, gst);
   }
 }
 
-// 3D y passes: independent lines l = (c*nz + z)*Hx + kx; src line stride ny (fwd) or Py (inv).
-template <bool INV>
-__global__ void __launch_bounds__(1024) y_pass_kernel(ColArgs a, const float2* __restrict__ tw) {
+// 3D y passes over independent lines l = (c*nz + z)*Hx + kx: forward S (ny) -> T (Py),
+// inverse T (Py) -> S (first ny).
+template <int L, bool INV>
+__global__ void __launch_bounds__(ypass_lines(L) * L / GBD_E, min_blocks(ypass_lines(L) * L / GBD_E))
+    y_pass_kernel(ColArgs a, const float2* __restrict__ tw) {
+  constexpr int LINES = ypass_lines(L);
+  constexpr int LS = line_stride<L, false>();
+  constexpr int NP = npasses(L, false);
   extern __shared__ float2 sm[];
-  const int C = a.C, Py = a.Py, LS = Py;
-  const long long l0 = (long long)blockIdx.x * C;
-  const int T = blockDim.x;
-  const int in_len = INV ? Py : a.ny;
-  const int out_len = INV ? a.ny : Py;
-  for (int e = threadIdx.x; e < C * Py; e += T) {
-    int line = e / Py;
-    int y = e - line * Py;
-    long long l = l0 + line;
-    float2 v = make_float2(0.f, 0.f);
-    if (y < in_len && l < a.lines_total) v = a.src[l * in_len + y];
-    sm[line * LS + y] = v;
-  }
-  __syncthreads();
-  fft_lines_smem<INV ? 1 : -1, false>(sm, Py, LS, C, tw);
-  for (int e = threadIdx.x; e < C * out_len; e += T) {
-    int line = e / out_len;
-    int y = e - line * out_len;
-    long long l = l0 + line;
-    if (l < a.lines_total) a.dst[l * out_len + y] = sm[line * LS + y];
+  const long long l0 = (long long)blockIdx.x * LINES;
+  const int ny = a.ny;
+  const long long nl = a.lines_total;
+  auto sld = [&](int line, int i) { return sm[line * LS + pad(i)]; };
+  auto sst = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
+  if constexpr (!INV) {
+    auto gld = [&](int line, int y) {
+      return (y < ny && l0 + line < nl) ? a.src[(l0 + line) * ny + y] : make_float2(0.f, 0.f);
+    };
+    auto gst = [&](int line, int i, float2 v) {
+      if (l0 + line < nl) a.dst[(l0 + line) * L + i] = v;
+    };
+    if constexpr (NP == 1) {
+      stockham_pass<-1, false, L, radix_at(L, false, 0), 1, LINES, false, false>(tw, gld, gst);
+    } else {
+      stockham_pass<-1, false, L, radix_at(L, false, 0), 1, LINES, false, false>(tw, gld, sst);
+      __syncthreads();
+      fwd_passes_smem<-1, L, false, LINES, false, 1, NP - 1>(sm, tw);
+      stockham_pass<-1, false, L, radix_at(L, false, NP - 1), ns_at(L, false, NP - 1), LINES, false, false>(tw, sld,
+                                                                                                           gst);
+    }
+  } else {
+    auto gld = [&](int line, int i) {
+      return (l0 + line < nl) ? a.src[(l0 + line) * L + i] : make_float2(0.f, 0.f);
+    };
+    auto gst = [&](int line, int y, float2 v) {
+      if (y < ny && l0 + line < nl) a.dst[(l0 + line) * ny + y] = v;
+    };
+    if constexpr (NP == 1) {
+      stockham_pass<1, true, L, radix_at(L, false, 0), 1, LINES, false, false>(tw, gld, gst);
+    } else {
+      stockham_pass<1, true, L, radix_at(L, false, NP - 1), ns_at(L, false, NP - 1), LINES, false, false>(tw, gld,
+                                                                                                         sst);
+      __syncthreads();
+      adj_passes_smem<1, L, false, LINES, false, NP - 1, 1>(sm, tw);
+      stockham_pass<1, true, L, radix_at(L, false, 0), 1, LINES, false, false>(tw, sld, gst);
+    }
   }
 }
 
-// 3D z convolution: block = C consecutive columns q of [3][nz][Q]; lines interleaved.
-__global__ void __launch_bounds__(1024) z_conv_kernel(ColArgs a, const float2* __restrict__ tw) {
+// 3D z convolution: block = W consecutive columns q of [3][nz][Q], lines c * W + w,
+// interleaved (consecutive threads take consecutive columns).
+template <int L>
+__global__ void __launch_bounds__(3 * zconv_cols(L) * L / GBD_E, min_blocks(3 * zconv_cols(L) * L / GBD_E))
+    z_conv_kernel(ColArgs a, const float2* __restrict__ tw) {
+  constexpr int W = zconv_cols(L);
+  constexpr int LINES = 3 * W;
+  constexpr int T = LINES * L / GBD_E;
+  constexpr int LS = line_stride<L, true>();
+  constexpr int NP = npasses(L, true);
+  constexpr int RL = radix_at(L, true, NP - 1);
+  constexpr int NSL = ns_at(L, true, NP - 1);
+  constexpr int LR = L / RL;
+  constexpr int KZ = L / 2 + 1;
   extern __shared__ float2 sm[];
-  const int W = a.C, Pz = a.Pz, LS = Pz + 1;
-  const int lines = 3 * W;
   const long long q0 = (long long)blockIdx.x * W;
-  const int T = blockDim.x;
+  const int nz = a.nz;
+  const long long Q = a.Q;
   float2* D = a.dst;
-  for (int e = threadIdx.x; e < lines * Pz; e += T) {
-    int line = e % lines;
-    int z = e / lines;
-    int c = line / W, w = line - c * W;
-    long long q = q0 + w;
-    float2 v = make_float2(0.f, 0.f);
-    if (z < a.nz && q < a.Q) v = D[(long long)(c * a.nz + z) * a.Q + q];
-    sm[line * LS + z] = v;
-  }
-  __syncthreads();
-  fft_lines_smem<-1, true>(sm, Pz, LS, lines, tw);
-  const int Ky = a.Py / 2 + 1, Kz = Pz / 2 + 1;
-  for (int e = threadIdx.x; e < W * Pz; e += T) {
-    int w = e % W;
-    int kz = e / W;
-    long long q = q0 + w;
-    if (q >= a.Q) continue;
-    int kx = (int)(q / a.Pyq);
-    int ky = (int)(q - (long long)kx * a.Pyq);
-    int kyp = ky, kzp = kz;
-    float sy = 1.f, sz = 1.f;
-    if (a.Py > 1 && ky > a.Py / 2) {
-      kyp = a.Py - ky;
-      sy = -1.f;
+  auto gld = [&](int line, int z) {
+    const long long q = q0 + line % W;
+    return (z < nz && q < Q) ? D[(long long)((line / W) * nz + z) * Q + q] : make_float2(0.f, 0.f);
+  };
+  auto gst = [&](int line, int z, float2 v) {
+    const long long q = q0 + line % W;
+    if (z < nz && q < Q) D[(long long)((line / W) * nz + z) * Q + q] = v;
+  };
+  auto sld = [&](int line, int i) { return sm[line * LS + pad(i)]; };
+  auto sst = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
+  const int Py = a.Py, KY = a.Py / 2 + 1, Pyq = a.Pyq;
+  auto run_fused = [&](auto ld, auto st) {
+    for (int it = threadIdx.x; it < W * LR; it += T) {
+      const int w = it % W, j = it / W;
+      const long long q = q0 + w;
+      const int kx = (int)(q / Pyq);
+      const int ky = (int)(q - (long long)kx * Pyq);
+      int kyp = ky;
+      float sy = 1.f;
+      if (Py > 1 && ky > Py / 2) {
+        kyp = Py - ky;
+        sy = -1.f;
+      }
+      const float* kbase = a.K3 + ((long long)kx * KY + kyp) * KZ * 6;
+      auto mul = [&](int kz, float2& m0, float2& m1, float2& m2) {
+        if (q >= Q) return;
+        int kzp = kz;
+        float sz = 1.f;
+        if (kz > L / 2) {
+          kzp = L - kz;
+          sz = -1.f;
+        }
+        const float* kp = kbase + kzp * 6;
+        const float2 k01 = __ldg(reinterpret_cast<const float2*>(kp));
+        const float2 k23 = __ldg(reinterpret_cast<const float2*>(kp + 2));
+        const float2 k45 = __ldg(reinterpret_cast<const float2*>(kp + 4));
+        const float kxx = k01.x, kyy = k01.y, kzz = k23.x;
+        const float kxy = sy * k23.y, kxz = sz * k45.x, kyz = sy * sz * k45.y;
+        const float2 h0 = make_float2(kxx * m0.x + kxy * m1.x + kxz * m2.x, kxx * m0.y + kxy * m1.y + kxz * m2.y);
+        const float2 h1 = make_float2(kxy * m0.x + kyy * m1.x + kyz * m2.x, kxy * m0.y + kyy * m1.y + kyz * m2.y);
+        const float2 h2 = make_float2(kxz * m0.x + kyz * m1.x + kzz * m2.x, kxz * m0.y + kyz * m1.y + kzz * m2.y);
+        m0 = h0;
+        m1 = h1;
+        m2 = h2;
+      };
+      fused_item<L, RL, NSL>(w, W, j, tw, ld, st, mul);
     }
-    if (Pz > 1 && kz > Pz / 2) {
-      kzp = Pz - kz;
-      sz = -1.f;
+  };
+  if constexpr (NP == 1) {
+    run_fused(gld, gst);
+  } else {
+    stockham_pass<-1, false, L, radix_at(L, true, 0), 1, LINES, true, false>(tw, gld, sst);
+    __syncthreads();
+    fwd_passes_smem<-1, L, true, LINES, true, 1, NP - 1>(sm, tw);
+    run_fused(sld, sst);
+    __syncthreads();
+    adj_passes_smem<1, L, true, LINES, true, NP - 1, 1>(sm, tw);
+    stockham_pass<1, true, L, radix_at(L, true, 0), 1, LINES, true, false>(tw, sld, gst);
+  }
+}
+
+// ---- launchers ------------------------------------------------------------------------------
+
+template <class K>
+static void prep(K k, size_t smem) {
+  static thread_local const void* done[64] = {nullptr};
+  for (auto& d : done) {
+    if (d == (const void*)k) return;
+    if (d == nullptr) {
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      d = (const void*)k;
+      return;
     }
-    const float* kp = a.K3 + (((long long)kx * Ky + kyp) * Kz + kzp) * 6;
-    float kxx = __ldg(kp), kyy = __ldg(kp + 1), kzz = __ldg(kp + 2);
-    float kxy = sy * __ldg(kp + 3), kxz = sz * __ldg(kp + 4), kyz = sy * sz * __ldg(kp + 5);
-    float2 m0 = sm[(0 * W + w) * LS + kz], m1 = sm[(1 * W + w) * LS + kz], m2 = sm[(2 * W + w) * LS + kz];
-    sm[(0 * W + w) * LS + kz] = make_float2(kxx * m0.x + kxy * m1.x + kxz * m2.x, kxx * m0.y + kxy * m1.y + kxz * m2.y);
-    sm[(1 * W + w) * LS + kz] = make_float2(kxy * m0.x + kyy * m1.x + kyz * m2.x, kxy * m0.y + kyy * m1.y + kyz * m2.y);
-    sm[(2 * W + w) * LS + kz] = make_float2(kxz * m0.x + kyz * m1.x + kzz * m2.x, kxz * m0.y + kyz * m1.y + kzz * m2.y);
   }
-  __syncthreads();
-  fft_lines_smem<1, true>(sm, Pz, LS, lines, tw);
-  for (int e = threadIdx.x; e < lines * a.nz; e += T) {
-    int line = e % lines;
-    int z = e / lines;
-    int c = line / W, w = line - c * W;
-    long long q = q0 + w;
-    if (q < a.Q) D[(long long)(c * a.nz + z) * a.Q + q] = sm[line * LS + z];
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int LX>
+static void row_launch_t(const RowArgs& a, const float2* tw, cudaStream_t st) {
+  constexpr int RB = row_rb(LX);
+  constexpr int T = 3 * RB * LX / GBD_E;
+  const size_t smem = (size_t)3 * RB * line_stride<LX, false>() * sizeof(float2);
+  prep(row_kernel<LX>, smem);
+  row_kernel<LX><<<(a.rows + RB - 1) / RB, T, smem, st>>>(a, tw);
+}
+
+template <int L>
+static void film_launch_t(const ColArgs& a, const float2* tw, cudaStream_t st) {
+  constexpr int C = film_cols(L);
+  constexpr int T = 3 * C * L / GBD_E;
+  const size_t smem = (size_t)3 * C * line_stride<L, false>() * sizeof(float2);
+  prep(film_conv_kernel<L>, smem);
+  film_conv_kernel<L><<<(a.Hx + C - 1) / C, T, smem, st>>>(a, tw);
+}
+
+template <int L, bool INV>
+static void ypass_launch_t(const ColArgs& a, const float2* tw, cudaStream_t st) {
+  constexpr int C = ypass_lines(L);
+  constexpr int T = C * L / GBD_E;
+  const size_t smem = (size_t)C * line_stride<L, false>() * sizeof(float2);
+  prep(y_pass_kernel<L, INV>, smem);
+  y_pass_kernel<L, INV><<<(unsigned)((a.lines_total + C - 1) / C), T, smem, st>>>(a, tw);
+}
+
+template <int L>
+static void zconv_launch_t(const ColArgs& a, const float2* tw, cudaStream_t st) {
+  constexpr int W = zconv_cols(L);
+  constexpr int T = 3 * W * L / GBD_E;
+  const size_t smem = (size_t)3 * W * line_stride<L, true>() * sizeof(float2);
+  prep(z_conv_kernel<L>, smem);
+  z_conv_kernel<L><<<(unsigned)((a.Q + W - 1) / W), T, smem, st>>>(a, tw);
+}
+
+bool launch_row(int Lx, const RowArgs& a, const float2* tw, cudaStream_t st) {
+  switch (Lx) {
+    case 1: row_launch_t<1>(a, tw, st); return true;
+    case 2: row_launch_t<2>(a, tw, st); return true;
+    case 4: row_launch_t<4>(a, tw, st); return true;
+    case 8: row_launch_t<8>(a, tw, st); return true;
+    case 16: row_launch_t<16>(a, tw, st); return true;
+    case 32: row_launch_t<32>(a, tw, st); return true;
+    case 64: row_launch_t<64>(a, tw, st); return true;
+    case 128: row_launch_t<128>(a, tw, st); return true;
+    case 256: row_launch_t<256>(a, tw, st); return true;
+    case 512: row_launch_t<512>(a, tw, st); return true;
+    case 1024: row_launch_t<1024>(a, tw, st); return true;
+    case 2048: row_launch_t<2048>(a, tw, st); return true;
+    case 4096: row_launch_t<4096>(a, tw, st); return true;
+    default: return false;
   }
 }
 
-static void set_smem(const void* k, size_t smem) {
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+bool launch_film_conv(const ColArgs& a, const float2* tw, cudaStream_t st) {
+  switch (a.Py) {
+    case 1: film_launch_t<1>(a, tw, st); return true;
+    case 4: film_launch_t<4>(a, tw, st); return true;
+    case 8: film_launch_t<8>(a, tw, st); return true;
+    case 16: film_launch_t<16>(a, tw, st); return true;
+    case 32: film_launch_t<32>(a, tw, st); return true;
+    case 64: film_launch_t<64>(a, tw, st); return true;
+    case 128: film_launch_t<128>(a, tw, st); return true;
+    case 256: film_launch_t<256>(a, tw, st); return true;
+    case 512: film_launch_t<512>(a, tw, st); return true;
+    case 1024: film_launch_t<1024>(a, tw, st); return true;
+    case 2048: film_launch_t<2048>(a, tw, st); return true;
+    case 4096: film_launch_t<4096>(a, tw, st); return true;
+    default: return false;
+  }
 }
 
-void launch_film_conv(const ColArgs& a, const float2* tw, cudaStream_t st) {
-  size_t smem = (size_t)3 * a.C * a.Py * sizeof(float2);
-  set_smem((const void*)film_conv_kernel, smem);
-  int blocks = (a.Hx + a.C - 1) / a.C;
-  film_conv_kernel<<<blocks, 3 * a.C * a.Py / GBD_E, smem, st>>>(a, tw);
+template <bool INV>
+static bool ypass_dispatch(const ColArgs& a, const float2* tw, cudaStream_t st) {
+  switch (a.Py) {
+    case 4: ypass_launch_t<4, INV>(a, tw, st); return true;
+    case 8: ypass_launch_t<8, INV>(a, tw, st); return true;
+    case 16: ypass_launch_t<16, INV>(a, tw, st); return true;
+    case 32: ypass_launch_t<32, INV>(a, tw, st); return true;
+    case 64: ypass_launch_t<64, INV>(a, tw, st); return true;
+    case 128: ypass_launch_t<128, INV>(a, tw, st); return true;
+    case 256: ypass_launch_t<256, INV>(a, tw, st); return true;
+    case 512: ypass_launch_t<512, INV>(a, tw, st); return true;
+    case 1024: ypass_launch_t<1024, INV>(a, tw, st); return true;
+    case 2048: ypass_launch_t<2048, INV>(a, tw, st); return true;
+    case 4096: ypass_launch_t<4096, INV>(a, tw, st); return true;
+    default: return false;
+  }
 }
 
-void launch_y_fwd(const ColArgs& a, const float2* tw, cudaStream_t st) {
-  size_t smem = (size_t)a.C * a.Py * sizeof(float2);
-  set_smem((const void*)y_pass_kernel<false>, smem);
-  int blocks = (a.lines_total + a.C - 1) / a.C;
-  y_pass_kernel<false><<<blocks, a.C * a.Py / GBD_E, smem, st>>>(a, tw);
-}
+bool launch_y_fwd(const ColArgs& a, const float2* tw, cudaStream_t st) { return ypass_dispatch<false>(a, tw, st); }
+bool launch_y_inv(const ColArgs& a, const float2* tw, cudaStream_t st) { return ypass_dispatch<true>(a, tw, st); }
 
-void launch_y_inv(const ColArgs& a, const float2* tw, cudaStream_t st) {
-  size_t smem = (size_t)a.C * a.Py * sizeof(float2);
-  set_smem((const void*)y_pass_kernel<true>, smem);
-  int blocks = (a.lines_total + a.C - 1) / a.C;
-  y_pass_kernel<true><<<blocks, a.C * a.Py / GBD_E, smem, st>>>(a, tw);
-}
-
-void launch_z_conv(const ColArgs& a, const float2* tw, cudaStream_t st) {
-  size_t smem = (size_t)3 * a.C * (a.Pz + 1) * sizeof(float2);
-  set_smem((const void*)z_conv_kernel, smem);
-  long long blocks = (a.Q + a.C - 1) / a.C;
-  z_conv_kernel<<<(unsigned)blocks, 3 * a.C * a.Pz / GBD_E, smem, st>>>(a, tw);
+bool launch_z_conv(const ColArgs& a, const float2* tw, cudaStream_t st) {
+  switch (a.Pz) {
+    case 4: zconv_launch_t<4>(a, tw, st); return true;
+    case 8: zconv_launch_t<8>(a, tw, st); return true;
+    case 16: zconv_launch_t<16>(a, tw, st); return true;
+    case 32: zconv_launch_t<32>(a, tw, st); return true;
+    case 64: zconv_launch_t<64>(a, tw, st); return true;
+    case 128: zconv_launch_t<128>(a, tw, st); return true;
+    case 256: zconv_launch_t<256>(a, tw, st); return true;
+    case 512: zconv_launch_t<512>(a, tw, st); return true;
+    case 1024: zconv_launch_t<1024>(a, tw, st); return true;
+    case 2048: zconv_launch_t<2048>(a, tw, st); return true;
+    case 4096: zconv_launch_t<4096>(a, tw, st); return true;
+    default: return false;
+  }
 }
 
 }  // namespace gbd

@@ -1,4 +1,4 @@
-// Kernel argument blocks and launch helpers for the demag / LLG passes.
+// Kernel argument blocks, block shapes and launch helpers for the demag / LLG passes.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -16,12 +16,17 @@ enum RowMode : int {
   ROW_RK4 = 7,
 };
 
+// Block shapes, shared by host planning and the kernels (L = transform length).
+__host__ __device__ constexpr int row_rb(int Lx) { return Lx >= 2048 ? 1 : 2048 / Lx; }  // rows per block
+__host__ __device__ constexpr int film_cols(int Py) { return Py >= 1024 ? 1 : 1024 / Py; }
+__host__ __device__ constexpr int ypass_lines(int Py) { return Py >= 4096 ? 1 : 4096 / Py; }
+__host__ __device__ constexpr int zconv_cols(int Pz) { return Pz >= 2048 ? 1 : 2048 / Pz; }
+
 struct RowArgs {
-  int nx, Lx, Hx, ny, nz;   // Lx = Px / 2, Hx = Lx + 1
+  int nx, ny, nz;           // mesh
   int rows;                 // ny * nz
-  int RB;                   // rows per block
-  int tw_stride;            // GBD_TW_LEN / Px
   long long N;              // cells
+  int mode, fwd_after;      // RowMode; run the forward transform of the next stage
   const float* in;          // ROW_FWD input, planar [3][nz][ny][nx]
   float2* S;                // x spectrum [3][nz][Hx][ny]
   float* out;               // ROW_H / ROW_HEFF / ROW_RHS output, planar
@@ -39,24 +44,21 @@ struct RowArgs {
 
 struct ColArgs {
   int Hx, ny, nz, Py, Pz;
-  int lines_total;          // number of independent lines (y passes)
-  int C;                    // columns (or lines) per block
-  int tw_stride_y, tw_stride_z;
+  long long lines_total;    // y passes: 3 * nz * Hx independent lines
   const float2* src;
   float2* dst;
   const float4* Kf;         // film kernel [Hx][Py/2+1] (xx, yy, zz, xy)
   const float* K3;          // 3D kernel [Hx][Py/2+1][Pz/2+1][6]
-  long long Q;              // z-conv columns = Hx * Py (or Hx when ny == 1)
-  int Pyq;                  // y extent of the z-conv column index (Py, or 1 when ny == 1)
+  long long Q;              // z-conv columns per plane = Hx * Py (Hx when ny == 1)
+  int Pyq;                  // y extent of the column index q (Py, or 1 when ny == 1)
 };
 
-size_t row_smem_bytes(int RB, int Lx);
-int row_threads(int RB, int Lx);
-
-void launch_row(int mode, bool fwd_after, const RowArgs& a, const float2* tw, cudaStream_t st);
-void launch_film_conv(const ColArgs& a, const float2* tw, cudaStream_t st);
-void launch_y_fwd(const ColArgs& a, const float2* tw, cudaStream_t st);
-void launch_y_inv(const ColArgs& a, const float2* tw, cudaStream_t st);
-void launch_z_conv(const ColArgs& a, const float2* tw, cudaStream_t st);
+// Launchers dispatch on the transform length (a power of two); they return false for a
+// length without an instantiation.
+bool launch_row(int Lx, const RowArgs& a, const float2* tw, cudaStream_t st);
+bool launch_film_conv(const ColArgs& a, const float2* tw, cudaStream_t st);
+bool launch_y_fwd(const ColArgs& a, const float2* tw, cudaStream_t st);
+bool launch_y_inv(const ColArgs& a, const float2* tw, cudaStream_t st);
+bool launch_z_conv(const ColArgs& a, const float2* tw, cudaStream_t st);
 
 }  // namespace gbd
