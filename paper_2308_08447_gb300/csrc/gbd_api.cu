@@ -11,7 +11,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/gbdemag.h"
+#include "gbdemag.h"
 #include "gbd_fft.cuh"
 #include "gbd_kernels.cuh"
 #include "gbd_plan.h"

@@ -155,27 +155,39 @@ __device__ __forceinline__ void dft(float2* x) {
   }
 }
 
-// w[r] = exp(S 2 pi i r k / (Ns R)), r in [0, R), from loads of w^1, w^2, w^4, w^8.
+// v[r] *= exp(S 2 pi i r k / (Ns R)) for r in [1, R): loads w, w^2, w^4, w^8 and forms each
+// other power right before use (w^3 = w w^2, w^(8+r) = w^r w^8, ...), so at most the base
+// powers and one product are live next to the data.
 template <int S, int R, int Ns>
-__device__ __forceinline__ void twiddles(const float2* __restrict__ tw, int k, float2* w) {
+__device__ __forceinline__ void apply_twiddles(float2* v, int k, const float2* __restrict__ tw) {
   constexpr int step = GBD_TW_LEN / (Ns * R);
   const int m = k * step;
-  w[0] = make_float2(1.f, 0.f);
-  w[1] = twiddle<S>(tw, m);
+  const float2 w1 = twiddle<S>(tw, m);
+  v[1] = cmul(v[1], w1);
   if constexpr (R >= 4) {
-    w[2] = twiddle<S>(tw, 2 * m);
-    w[3] = cmul(w[1], w[2]);
-  }
-  if constexpr (R >= 8) {
-    w[4] = twiddle<S>(tw, 4 * m);
-    w[5] = cmul(w[1], w[4]);
-    w[6] = cmul(w[2], w[4]);
-    w[7] = cmul(w[3], w[4]);
-  }
-  if constexpr (R >= 16) {
-    w[8] = twiddle<S>(tw, 8 * m);
-#pragma unroll
-    for (int r = 1; r < 8; ++r) w[8 + r] = cmul(w[r], w[8]);
+    const float2 w2 = twiddle<S>(tw, 2 * m);
+    const float2 w3 = cmul(w1, w2);
+    v[2] = cmul(v[2], w2);
+    v[3] = cmul(v[3], w3);
+    if constexpr (R >= 8) {
+      const float2 w4 = twiddle<S>(tw, 4 * m);
+      const float2 w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
+      v[4] = cmul(v[4], w4);
+      v[5] = cmul(v[5], w5);
+      v[6] = cmul(v[6], w6);
+      v[7] = cmul(v[7], w7);
+      if constexpr (R >= 16) {
+        const float2 w8 = twiddle<S>(tw, 8 * m);
+        v[8] = cmul(v[8], w8);
+        v[9] = cmul(v[9], cmul(w1, w8));
+        v[10] = cmul(v[10], cmul(w2, w8));
+        v[11] = cmul(v[11], cmul(w3, w8));
+        v[12] = cmul(v[12], cmul(w4, w8));
+        v[13] = cmul(v[13], cmul(w5, w8));
+        v[14] = cmul(v[14], cmul(w6, w8));
+        v[15] = cmul(v[15], cmul(w7, w8));
+      }
+    }
   }
 }
 
@@ -183,21 +195,11 @@ __device__ __forceinline__ void twiddles(const float2* __restrict__ tw, int k, f
 template <int S, int R, int Ns, bool ADJ>
 __device__ __forceinline__ void butterfly(float2* v, int k, const float2* __restrict__ tw) {
   if constexpr (!ADJ) {
-    if constexpr (Ns > 1) {
-      float2 w[R];
-      twiddles<S, R, Ns>(tw, k, w);
-#pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r]);
-    }
+    if constexpr (Ns > 1) apply_twiddles<S, R, Ns>(v, k, tw);
     dft<R, S>(v);
   } else {
     dft<R, S>(v);
-    if constexpr (Ns > 1) {
-      float2 w[R];
-      twiddles<S, R, Ns>(tw, k, w);
-#pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r]);
-    }
+    if constexpr (Ns > 1) apply_twiddles<S, R, Ns>(v, k, tw);
   }
 }
 
@@ -241,33 +243,32 @@ __device__ __forceinline__ void stockham_pass(const float2* __restrict__ tw, LD 
   }
 }
 
-// Passes [P0, P1) of the forward chain (sign S) in place in shared memory.
-template <int S, int L, bool CONV, int LINES, bool LF, int P, int PEND>
+// Passes [P, PEND) of the forward chain (sign S) in place in shared memory; LS is the
+// caller's line stride in float2 units.
+template <int S, int L, bool CONV, int LINES, bool LF, int LS, int P, int PEND>
 __device__ __forceinline__ void fwd_passes_smem(float2* sm, const float2* __restrict__ tw) {
   if constexpr (P < PEND) {
     constexpr int R = radix_at(L, CONV, P);
     constexpr int Ns = ns_at(L, CONV, P);
-    constexpr int LS = line_stride<L, LF>();
     auto ld = [&](int line, int i) { return sm[line * LS + pad(i)]; };
     auto st = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
     stockham_pass<S, false, L, R, Ns, LINES, LF, true>(tw, ld, st);
     __syncthreads();
-    fwd_passes_smem<S, L, CONV, LINES, LF, P + 1, PEND>(sm, tw);
+    fwd_passes_smem<S, L, CONV, LINES, LF, LS, P + 1, PEND>(sm, tw);
   }
 }
 
 // Adjoint passes P-1 down to PEND (inclusive) in place in shared memory.
-template <int S, int L, bool CONV, int LINES, bool LF, int P, int PEND>
+template <int S, int L, bool CONV, int LINES, bool LF, int LS, int P, int PEND>
 __device__ __forceinline__ void adj_passes_smem(float2* sm, const float2* __restrict__ tw) {
   if constexpr (P > PEND) {
     constexpr int R = radix_at(L, CONV, P - 1);
     constexpr int Ns = ns_at(L, CONV, P - 1);
-    constexpr int LS = line_stride<L, LF>();
     auto ld = [&](int line, int i) { return sm[line * LS + pad(i)]; };
     auto st = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
     stockham_pass<S, true, L, R, Ns, LINES, LF, true>(tw, ld, st);
     __syncthreads();
-    adj_passes_smem<S, L, CONV, LINES, LF, P - 1, PEND>(sm, tw);
+    adj_passes_smem<S, L, CONV, LINES, LF, LS, P - 1, PEND>(sm, tw);
   }
 }
 

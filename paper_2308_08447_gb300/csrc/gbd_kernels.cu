@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(3 * row_rb(LX) * LX / GBD_E, min_blocks(3 * ro
   constexpr int RB = row_rb(LX);
   constexpr int LINES = 3 * RB;
   constexpr int T = LINES * LX / GBD_E;
-  constexpr int LS = line_stride<LX, false>();
+  constexpr int LS = line_stride<LX, true>();  // odd: the rows' lines fall on different banks
   constexpr int NP = npasses(LX, false);
   constexpr int HX = LX + 1;
   constexpr int HALF = LX / 2;
@@ -45,38 +45,94 @@ __global__ void __launch_bounds__(3 * row_rb(LX) * LX / GBD_E, min_blocks(3 * ro
   const long long N = a.N;
   const int mode = a.mode;
   const int nx = a.nx, ny = a.ny;
+  // (z, y) of the block's first row; when the block's rows share a z plane (ny a multiple
+  // of RB, always for the power-of-two meshes) the per-element division is skipped
+  const int zb = r0 / ny, yb = r0 - zb * ny;
+  const bool one_plane = (yb + RB <= ny);
+  auto row_zy = [&](int rr, int& z, int& y) {
+    if (one_plane) {
+      z = zb;
+      y = yb + rr;
+    } else {
+      z = (r0 + rr) / ny;
+      y = r0 + rr - z * ny;
+    }
+  };
+  const float* __restrict__ ms = a.ms;
+  // rows per vector access of the [kx][y] spectrum: two adjacent rows are one 16-byte access
+  constexpr int VR = (RB % 2 == 0) ? 2 : 1;
+  constexpr int RG = RB / VR;
+  const bool vec = (VR == 2) && one_plane && (ny % 2 == 0);
 
   if (mode != ROW_FWD) {
-    // 1. X (global, [kx][y] layout) -> Z pairwise into shared memory; rows fastest.
-    for (int e = threadIdx.x; e < RB * 3 * (HALF + 1); e += T) {
-      const int rr = e % RB;
-      const int t2 = e / RB;
+    // 1. X (global, [kx][y] layout) -> Z pairwise into shared memory. An item is (row group,
+    //    component, k) with VR adjacent rows per group, read as one 16-byte vector when the
+    //    rows are adjacent in memory; every thread issues all its loads before using any.
+    constexpr int ITEMS = RG * 3 * (HALF + 1);
+    constexpr int IPT = (ITEMS + T - 1) / T;
+    float2 A[IPT][VR], B[IPT][VR];
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      const int e = threadIdx.x + i * T;
+      const int g = e % RG;
+      const int t2 = e / RG;
       const int c = t2 % 3;
       const int k = t2 / 3;
-      const int row = r0 + rr;
-      float2 zk = make_float2(0.f, 0.f), zl = zk;
-      if (row < a.rows) {
-        const int z = row / ny, y = row - z * ny;
-        const float2* base = a.S + (long long)(c * a.nz + z) * HX * ny + y;
-        const float2 A = base[(long long)k * ny];
-        const float2 B = base[(long long)(LX - k) * ny];
-        if (k == 0) {
-          zk = cadd(cadd(A, cconj(B)), cmul_i<1>(csub(A, cconj(B))));
+#pragma unroll
+      for (int u = 0; u < VR; ++u) A[i][u] = B[i][u] = make_float2(0.f, 0.f);
+      if (e < ITEMS) {
+        if (vec) {
+          const float2* base = a.S + (long long)(c * a.nz + zb) * HX * ny + yb + g * VR;
+          const float4 va = *reinterpret_cast<const float4*>(base + (long long)k * ny);
+          const float4 vb = *reinterpret_cast<const float4*>(base + (long long)(LX - k) * ny);
+          A[i][0] = make_float2(va.x, va.y);
+          A[i][VR - 1] = make_float2(va.z, va.w);
+          B[i][0] = make_float2(vb.x, vb.y);
+          B[i][VR - 1] = make_float2(vb.z, vb.w);
         } else {
-          const float2 wp = twiddle<-1>(tw, k * TWS);  // W^k
-          const float2 wm = cconj(wp);                  // W^-k
-          zk = cadd(cadd(A, cconj(B)), cmul_i<1>(cmul(wm, csub(A, cconj(B)))));
-          zl = csub(cadd(B, cconj(A)), cmul_i<1>(cmul(wp, csub(B, cconj(A)))));
+#pragma unroll
+          for (int u = 0; u < VR; ++u) {
+            const int rr = g * VR + u;
+            if (r0 + rr < a.rows) {
+              int z, y;
+              row_zy(rr, z, y);
+              const float2* base = a.S + (long long)(c * a.nz + z) * HX * ny + y;
+              A[i][u] = base[(long long)k * ny];
+              B[i][u] = base[(long long)(LX - k) * ny];
+            }
+          }
         }
       }
-      float2* L = sm + (c * RB + rr) * LS;
-      L[pad(k)] = zk;
-      if (k != 0 && k != LX - k) L[pad(LX - k)] = zl;
+    }
+#pragma unroll
+    for (int i = 0; i < IPT; ++i) {
+      const int e = threadIdx.x + i * T;
+      if (ITEMS % T != 0 && e >= ITEMS) break;
+      const int g = e % RG;
+      const int t2 = e / RG;
+      const int c = t2 % 3;
+      const int k = t2 / 3;
+      const float2 wp = twiddle<-1>(tw, k * TWS);  // W^k
+      const float2 wm = cconj(wp);                  // W^-k
+#pragma unroll
+      for (int u = 0; u < VR; ++u) {
+        const float2 Au = A[i][u], Bu = B[i][u];
+        float2 zk, zl = make_float2(0.f, 0.f);
+        if (k == 0) {
+          zk = cadd(cadd(Au, cconj(Bu)), cmul_i<1>(csub(Au, cconj(Bu))));
+        } else {
+          zk = cadd(cadd(Au, cconj(Bu)), cmul_i<1>(cmul(wm, csub(Au, cconj(Bu)))));
+          zl = csub(cadd(Bu, cconj(Au)), cmul_i<1>(cmul(wp, csub(Bu, cconj(Au)))));
+        }
+        float2* L = sm + (c * RB + g * VR + u) * LS;
+        L[pad(k)] = zk;
+        if (k != 0 && k != LX - k) L[pad(LX - k)] = zl;
+      }
     }
     __syncthreads();
     // 2. unnormalised inverse FFT: adjoint passes, the last one keeping the lower half only.
     if constexpr (NP >= 1) {
-      adj_passes_smem<1, LX, false, LINES, false, NP, 1>(sm, tw);
+      adj_passes_smem<1, LX, false, LINES, false, LS, NP, 1>(sm, tw);
       auto ld = [&](int line, int i) { return sm[line * LS + pad(i)]; };
       auto st = [&](int line, int i, float2 v) {
         if (i < HALF) sm[line * LS + pad(i)] = v;
@@ -85,86 +141,190 @@ __global__ void __launch_bounds__(3 * row_rb(LX) * LX / GBD_E, min_blocks(3 * ro
       __syncthreads();
     }
     // 3. epilogue on the real rows: float view of line position x is 2 pad(x/2) + (x & 1).
-    for (int rr = 0; rr < RB; ++rr) {
-      const int row = r0 + rr;
-      if (row >= a.rows) break;
-      const int z = row / ny, y = row - z * ny;
-      for (int x = threadIdx.x; x < nx; x += T) {
-        const long long idx = (long long)row * nx + x;
+    float* __restrict__ out = a.out;
+    float* __restrict__ acc = a.acc;
+    float* __restrict__ mnext = a.mnext;
+    const float* __restrict__ m0 = a.m0;
+    float* __restrict__ m0_out = a.m0_out;  // aliases m0 in stage 4: each cell is read, then written, by one thread
+    // Per-cell update from the demag field hd, m and its Laplacian lap; m0v / accv are the
+    // cell's step-start m and k-sum (read only by the stages that need them). Returns the
+    // next stage's m in mn (stages) and writes the mode's global outputs through `put`.
+    auto update = [&](const float* hd, const float* m, const float* lap, const float* m0v, const float* accv,
+                      float* mn, float* acc_out, float* res) {
+      float H[3] = {hd[0] + lap[0] + a.hx, hd[1] + lap[1] + a.hy, hd[2] + lap[2] + a.hz};
+      if (mode == ROW_HEFF) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) res[c] = H[c];
+        return;
+      }
+      // dm/dt = -gamma/(1+alpha^2) [m x H + alpha m x (m x H)]
+      const float mxH[3] = {m[1] * H[2] - m[2] * H[1], m[2] * H[0] - m[0] * H[2], m[0] * H[1] - m[1] * H[0]};
+      const float mmH[3] = {m[1] * mxH[2] - m[2] * mxH[1], m[2] * mxH[0] - m[0] * mxH[2],
+                            m[0] * mxH[1] - m[1] * mxH[0]};
+      float f[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) f[c] = -a.geff * (mxH[c] + a.alpha * mmH[c]);
+      if (mode == ROW_RHS) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) res[c] = f[c];
+        return;
+      }
+      if (mode == ROW_RK1) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          acc_out[c] = f[c];
+          mn[c] = m[c] + 0.5f * a.dt * f[c];
+        }
+      } else if (mode == ROW_RK2 || mode == ROW_RK3) {
+        const float h = (mode == ROW_RK2) ? 0.5f * a.dt : a.dt;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          acc_out[c] = accv[c] + 2.f * f[c];
+          mn[c] = m0v[c] + h * f[c];
+        }
+      } else {  // ROW_RK4
+        const float h = a.dt * (1.0f / 6.0f);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) mn[c] = m0v[c] + h * (accv[c] + f[c]);
+        const float inv = rsqrtf(mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) mn[c] *= inv;
+      }
+    };
+    const bool need_m0 = (mode == ROW_RK2 || mode == ROW_RK3 || mode == ROW_RK4);
+    const long long sz = (long long)nx * ny;
+    if ((nx % 64) == 0) {
+      // Fast path: an item is a pair of cells (x0, x0 + 1); the 32 lanes of a warp take 32
+      // consecutive pairs of one row, so the x neighbours outside a pair come from the
+      // adjacent lanes. Loads and stores are 8-byte vectors.
+      const int NP2 = nx / 2;
+      for (int e = threadIdx.x; e < RB * NP2; e += T) {
+        const int rr = e / NP2;
+        const int xp = e - rr * NP2;
+        if (r0 + rr >= a.rows) continue;  // uniform per warp (NP2 is a multiple of 32)
+        int z, y;
+        row_zy(rr, z, y);
+        const int x0 = 2 * xp;
+        const long long idx = (long long)(r0 + rr) * nx + x0;
+        const int lane = threadIdx.x & 31;
+        float hd[2][3], mv[2][3], lap[2][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float2 h2 = sm[(c * RB + rr) * LS + pad(xp)];
+          hd[0][c] = h2.x * a.hscale;
+          hd[1][c] = h2.y * a.hscale;
+        }
+        if (mode == ROW_H) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) *reinterpret_cast<float2*>(out + c * N + idx) = make_float2(hd[0][c], hd[1][c]);
+          continue;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float* __restrict__ p = ms + c * N + idx;
+          const float2 cc = *reinterpret_cast<const float2*>(p);
+          const float2 ym = y > 0 ? *reinterpret_cast<const float2*>(p - nx) : cc;
+          const float2 yp = y < ny - 1 ? *reinterpret_cast<const float2*>(p + nx) : cc;
+          float2 zm = cc, zp = cc;
+          if (a.nz > 1) {
+            if (z > 0) zm = *reinterpret_cast<const float2*>(p - sz);
+            if (z < a.nz - 1) zp = *reinterpret_cast<const float2*>(p + sz);
+          }
+          float left = __shfl_up_sync(0xffffffffu, cc.y, 1);
+          float right = __shfl_down_sync(0xffffffffu, cc.x, 1);
+          if (lane == 0) left = x0 > 0 ? p[-1] : cc.x;
+          if (lane == 31) right = x0 + 2 < nx ? p[2] : cc.y;
+          mv[0][c] = cc.x;
+          mv[1][c] = cc.y;
+          lap[0][c] = a.cx * (left - 2.f * cc.x + cc.y) + a.cy * (ym.x - 2.f * cc.x + yp.x) + a.cz * (zm.x - 2.f * cc.x + zp.x);
+          lap[1][c] = a.cx * (cc.x - 2.f * cc.y + right) + a.cy * (ym.y - 2.f * cc.y + yp.y) + a.cz * (zm.y - 2.f * cc.y + zp.y);
+        }
+        float m0v[2][3] = {}, accv[2][3] = {};
+        if (need_m0) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float2 q0 = *reinterpret_cast<const float2*>(m0 + c * N + idx);
+            const float2 qa = *reinterpret_cast<const float2*>(acc + c * N + idx);
+            m0v[0][c] = q0.x;
+            m0v[1][c] = q0.y;
+            accv[0][c] = qa.x;
+            accv[1][c] = qa.y;
+          }
+        }
+        float mn[2][3], ao[2][3], res[2][3];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) update(hd[u], mv[u], lap[u], m0v[u], accv[u], mn[u], ao[u], res[u]);
+        if (mode == ROW_HEFF || mode == ROW_RHS) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) *reinterpret_cast<float2*>(out + c * N + idx) = make_float2(res[0][c], res[1][c]);
+          continue;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float2 v = make_float2(mn[0][c], mn[1][c]);
+          if (mode == ROW_RK4) {
+            *reinterpret_cast<float2*>(m0_out + c * N + idx) = v;
+          } else {
+            *reinterpret_cast<float2*>(acc + c * N + idx) = make_float2(ao[0][c], ao[1][c]);
+            *reinterpret_cast<float2*>(mnext + c * N + idx) = v;
+          }
+          if (a.fwd_after) sm[(c * RB + rr) * LS + pad(xp)] = v;
+        }
+      }
+    } else {
+      // General path: one cell per item.
+      for (int e = threadIdx.x; e < RB * nx; e += T) {
+        const int rr = e / nx;
+        const int x = e - rr * nx;
+        if (r0 + rr >= a.rows) continue;
+        int z, y;
+        row_zy(rr, z, y);
+        const long long idx = (long long)(r0 + rr) * nx + x;
         const int fpos = 2 * pad(x >> 1) + (x & 1);
-        float hd[3];
+        float hd[3], mv[3], lap[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) hd[c] = reinterpret_cast<const float*>(sm + (c * RB + rr) * LS)[fpos] * a.hscale;
         if (mode == ROW_H) {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) a.out[c * N + idx] = hd[c];
+          for (int c = 0; c < 3; ++c) out[c * N + idx] = hd[c];
           continue;
         }
         // exchange: 7-point Laplacian, free boundaries (missing neighbour = the cell itself)
-        const long long sy = nx, sz = (long long)nx * ny;
         const long long ixm = x > 0 ? idx - 1 : idx, ixp = x < nx - 1 ? idx + 1 : idx;
-        const long long iym = y > 0 ? idx - sy : idx, iyp = y < ny - 1 ? idx + sy : idx;
+        const long long iym = y > 0 ? idx - nx : idx, iyp = y < ny - 1 ? idx + nx : idx;
         const long long izm = z > 0 ? idx - sz : idx, izp = z < a.nz - 1 ? idx + sz : idx;
-        float m[3], H[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const float* p = a.ms + c * N;
+          const float* __restrict__ p = ms + c * N;
           const float mc = p[idx];
-          m[c] = mc;
-          const float lap = a.cx * (p[ixp] - 2.f * mc + p[ixm]) + a.cy * (p[iyp] - 2.f * mc + p[iym]) +
-                            a.cz * (p[izp] - 2.f * mc + p[izm]);
-          H[c] = hd[c] + lap;
+          mv[c] = mc;
+          lap[c] = a.cx * (p[ixp] - 2.f * mc + p[ixm]) + a.cy * (p[iyp] - 2.f * mc + p[iym]) +
+                   a.cz * (p[izp] - 2.f * mc + p[izm]);
         }
-        H[0] += a.hx;
-        H[1] += a.hy;
-        H[2] += a.hz;
-        if (mode == ROW_HEFF) {
+        float m0v[3] = {}, accv[3] = {};
+        if (need_m0) {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) a.out[c * N + idx] = H[c];
+          for (int c = 0; c < 3; ++c) {
+            m0v[c] = m0[c * N + idx];
+            accv[c] = acc[c * N + idx];
+          }
+        }
+        float mn[3], ao[3], res[3];
+        update(hd, mv, lap, m0v, accv, mn, ao, res);
+        if (mode == ROW_HEFF || mode == ROW_RHS) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) out[c * N + idx] = res[c];
           continue;
         }
-        // dm/dt = -gamma/(1+alpha^2) [m x H + alpha m x (m x H)]
-        const float mxH[3] = {m[1] * H[2] - m[2] * H[1], m[2] * H[0] - m[0] * H[2], m[0] * H[1] - m[1] * H[0]};
-        const float mmH[3] = {m[1] * mxH[2] - m[2] * mxH[1], m[2] * mxH[0] - m[0] * mxH[2],
-                              m[0] * mxH[1] - m[1] * mxH[0]};
-        float f[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) f[c] = -a.geff * (mxH[c] + a.alpha * mmH[c]);
-        if (mode == ROW_RHS) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) a.out[c * N + idx] = f[c];
-          continue;
-        }
-        float mn[3];
-        if (mode == ROW_RK1) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            a.acc[c * N + idx] = f[c];
-            mn[c] = m[c] + 0.5f * a.dt * f[c];
-            a.mnext[c * N + idx] = mn[c];
+        for (int c = 0; c < 3; ++c) {
+          if (mode == ROW_RK4) {
+            m0_out[c * N + idx] = mn[c];
+          } else {
+            acc[c * N + idx] = ao[c];
+            mnext[c * N + idx] = mn[c];
           }
-        } else if (mode == ROW_RK2 || mode == ROW_RK3) {
-          const float h = (mode == ROW_RK2) ? 0.5f * a.dt : a.dt;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            a.acc[c * N + idx] += 2.f * f[c];
-            mn[c] = a.m0[c * N + idx] + h * f[c];
-            a.mnext[c * N + idx] = mn[c];
-          }
-        } else {  // ROW_RK4
-          const float h = a.dt * (1.0f / 6.0f);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) mn[c] = a.m0[c * N + idx] + h * (a.acc[c * N + idx] + f[c]);
-          const float inv = rsqrtf(mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            mn[c] *= inv;
-            a.m0_out[c * N + idx] = mn[c];
-          }
-        }
-        if (a.fwd_after) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) reinterpret_cast<float*>(sm + (c * RB + rr) * LS)[fpos] = mn[c];
+          if (a.fwd_after) reinterpret_cast<float*>(sm + (c * RB + rr) * LS)[fpos] = mn[c];
         }
       }
     }
@@ -178,15 +338,38 @@ __global__ void __launch_bounds__(3 * row_rb(LX) * LX / GBD_E, min_blocks(3 * ro
       for (int x = x0 + threadIdx.x; x < FL; x += T) fl[2 * pad(x >> 1) + (x & 1)] = 0.f;
     }
   } else {
-    // forward only: the input rows into the float view, zero beyond nx
-    for (int e = threadIdx.x; e < LINES * FL; e += T) {
-      const int line = e / FL;
-      const int x = e % FL;
-      const int c = line / RB, rr = line % RB;
-      const int row = r0 + rr;
-      float v = 0.f;
-      if (x < nx && row < a.rows) v = a.in[c * N + (long long)row * nx + x];
-      reinterpret_cast<float*>(sm + line * LS)[2 * pad(x >> 1) + (x & 1)] = v;
+    // forward only: the input rows into the float view, zero beyond nx; pairs of samples
+    // are one complex slot, read as 8-byte vectors when nx is even
+    constexpr int PAIRS = LINES * (FL / 2);
+    constexpr int IPT = (PAIRS + T - 1) / T;
+    if (FL >= 2 && (nx % 2) == 0) {
+      float2 v[IPT];
+#pragma unroll
+      for (int i = 0; i < IPT; ++i) {
+        const int e = threadIdx.x + i * T;
+        const int line = e / (FL / 2);
+        const int xp = e % (FL / 2);
+        const int c = line / RB, rr = line % RB;
+        v[i] = make_float2(0.f, 0.f);
+        if (e < PAIRS && 2 * xp < nx && r0 + rr < a.rows)
+          v[i] = *reinterpret_cast<const float2*>(a.in + c * N + (long long)(r0 + rr) * nx + 2 * xp);
+      }
+#pragma unroll
+      for (int i = 0; i < IPT; ++i) {
+        const int e = threadIdx.x + i * T;
+        if (PAIRS % T != 0 && e >= PAIRS) break;
+        sm[(e / (FL / 2)) * LS + pad(e % (FL / 2))] = v[i];
+      }
+    } else {
+      for (int e = threadIdx.x; e < LINES * FL; e += T) {
+        const int line = e / FL;
+        const int x = e % FL;
+        const int c = line / RB, rr = line % RB;
+        const int row = r0 + rr;
+        float v = 0.f;
+        if (x < nx && row < a.rows) v = a.in[c * N + (long long)row * nx + x];
+        reinterpret_cast<float*>(sm + line * LS)[2 * pad(x >> 1) + (x & 1)] = v;
+      }
     }
   }
   __syncthreads();
@@ -196,31 +379,48 @@ __global__ void __launch_bounds__(3 * row_rb(LX) * LX / GBD_E, min_blocks(3 * ro
     auto st = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
     stockham_pass<-1, false, LX, radix_at(LX, false, 0), 1, LINES, false, true>(tw, ld, st);
     __syncthreads();
-    fwd_passes_smem<-1, LX, false, LINES, false, 1, NP>(sm, tw);
+    fwd_passes_smem<-1, LX, false, LINES, false, LS, 1, NP>(sm, tw);
   }
-  // 6. Z -> X pairwise and store the half spectrum (rows fastest for the [kx][y] layout).
-  for (int e = threadIdx.x; e < RB * 3 * (HALF + 1); e += T) {
-    const int rr = e % RB;
-    const int t2 = e / RB;
+  // 6. Z -> X pairwise and store the half spectrum, VR adjacent rows per item.
+  for (int e = threadIdx.x; e < RG * 3 * (HALF + 1); e += T) {
+    const int g = e % RG;
+    const int t2 = e / RG;
     const int c = t2 % 3;
     const int k = t2 / 3;
-    const int row = r0 + rr;
-    if (row >= a.rows) continue;
-    const int z = row / ny, y = row - z * ny;
-    const float2* L = sm + (c * RB + rr) * LS;
-    float2* base = a.S + (long long)(c * a.nz + z) * HX * ny + y;
-    if (k == 0) {
-      const float2 A = L[pad(0)];
-      base[0] = make_float2(A.x + A.y, 0.f);
-      base[(long long)LX * ny] = make_float2(A.x - A.y, 0.f);
+    const float2 wp = twiddle<-1>(tw, k * TWS);  // W^k
+    const float2 wm = cconj(wp);
+    float2 xk[VR], xl[VR];
+#pragma unroll
+    for (int u = 0; u < VR; ++u) {
+      const float2* L = sm + (c * RB + g * VR + u) * LS;
+      if (k == 0) {
+        const float2 A = L[pad(0)];
+        xk[u] = make_float2(A.x + A.y, 0.f);   // X[0]
+        xl[u] = make_float2(A.x - A.y, 0.f);   // X[Lx]
+      } else {
+        const float2 A = L[pad(k)], B = L[pad(LX - k)];
+        xk[u] = cscale(csub(cadd(A, cconj(B)), cmul_i<1>(cmul(wp, csub(A, cconj(B))))), 0.5f);
+        xl[u] = cscale(cadd(cadd(B, cconj(A)), cmul_i<1>(cmul(wm, csub(B, cconj(A))))), 0.5f);
+      }
+    }
+    const int kl = (k == 0) ? LX : LX - k;  // partner frequency written with xl
+    const bool two = (k == 0) || (LX - k != k);
+    if (vec) {
+      float2* base = a.S + (long long)(c * a.nz + zb) * HX * ny + yb + g * VR;
+      *reinterpret_cast<float4*>(base + (long long)k * ny) = make_float4(xk[0].x, xk[0].y, xk[VR - 1].x, xk[VR - 1].y);
+      if (two)
+        *reinterpret_cast<float4*>(base + (long long)kl * ny) = make_float4(xl[0].x, xl[0].y, xl[VR - 1].x, xl[VR - 1].y);
     } else {
-      const float2 A = L[pad(k)], B = L[pad(LX - k)];
-      const float2 wp = twiddle<-1>(tw, k * TWS);  // W^k
-      const float2 wm = cconj(wp);
-      const float2 xk = csub(cadd(A, cconj(B)), cmul_i<1>(cmul(wp, csub(A, cconj(B)))));
-      const float2 xl = cadd(cadd(B, cconj(A)), cmul_i<1>(cmul(wm, csub(B, cconj(A)))));
-      base[(long long)k * ny] = cscale(xk, 0.5f);
-      if (LX - k != k) base[(long long)(LX - k) * ny] = cscale(xl, 0.5f);
+#pragma unroll
+      for (int u = 0; u < VR; ++u) {
+        const int rr = g * VR + u;
+        if (r0 + rr >= a.rows) continue;
+        int z, y;
+        row_zy(rr, z, y);
+        float2* base = a.S + (long long)(c * a.nz + z) * HX * ny + y;
+        base[(long long)k * ny] = xk[u];
+        if (two) base[(long long)kl * ny] = xl[u];
+      }
     }
   }
 }
@@ -243,26 +443,12 @@ __device__ __forceinline__ void fused_item(int line0, int lstride, int j, const 
 #pragma unroll
     for (int r = 0; r < RL; ++r) v[c][r] = ld(line0 + c * lstride, j + r * LR);
   if constexpr (RL > 1) {
-    float2 w[RL];
-    if constexpr (NSL > 1) twiddles<-1, RL, NSL>(tw, j, w);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      if constexpr (NSL > 1) {
-#pragma unroll
-        for (int r = 1; r < RL; ++r) v[c][r] = cmul(v[c][r], w[r]);
-      }
-      dft<RL, -1>(v[c]);
-    }
+    for (int c = 0; c < 3; ++c) butterfly<-1, RL, NSL, false>(v[c], j, tw);
 #pragma unroll
     for (int q = 0; q < RL; ++q) mul(j + q * LR, v[0][q], v[1][q], v[2][q]);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      dft<RL, 1>(v[c]);
-      if constexpr (NSL > 1) {
-#pragma unroll
-        for (int r = 1; r < RL; ++r) v[c][r] = cmul(v[c][r], cconj(w[r]));
-      }
-    }
+    for (int c = 0; c < 3; ++c) butterfly<1, RL, NSL, true>(v[c], j, tw);
   } else {
     mul(j, v[0][0], v[1][0], v[2][0]);
   }
@@ -329,10 +515,10 @@ __global__ void __launch_bounds__(3 * film_cols(L) * L / GBD_E, min_blocks(3 * f
   } else {
     stockham_pass<-1, false, L, radix_at(L, true, 0), 1, LINES, false, false>(tw, gld, sst);
     __syncthreads();
-    fwd_passes_smem<-1, L, true, LINES, false, 1, NP - 1>(sm, tw);
+    fwd_passes_smem<-1, L, true, LINES, false, LS, 1, NP - 1>(sm, tw);
     run_fused(sld, sst);
     __syncthreads();
-    adj_passes_smem<1, L, true, LINES, false, NP - 1, 1>(sm, tw);
+    adj_passes_smem<1, L, true, LINES, false, LS, NP - 1, 1>(sm, tw);
     stockham_pass<1, true, L, radix_at(L, true, 0), 1, LINES, false, false>(tw, sld, gst);
   }
 }
@@ -363,7 +549,7 @@ __global__ void __launch_bounds__(ypass_lines(L) * L / GBD_E, min_blocks(ypass_l
     } else {
       stockham_pass<-1, false, L, radix_at(L, false, 0), 1, LINES, false, false>(tw, gld, sst);
       __syncthreads();
-      fwd_passes_smem<-1, L, false, LINES, false, 1, NP - 1>(sm, tw);
+      fwd_passes_smem<-1, L, false, LINES, false, LS, 1, NP - 1>(sm, tw);
       stockham_pass<-1, false, L, radix_at(L, false, NP - 1), ns_at(L, false, NP - 1), LINES, false, false>(tw, sld,
                                                                                                            gst);
     }
@@ -380,7 +566,7 @@ __global__ void __launch_bounds__(ypass_lines(L) * L / GBD_E, min_blocks(ypass_l
       stockham_pass<1, true, L, radix_at(L, false, NP - 1), ns_at(L, false, NP - 1), LINES, false, false>(tw, gld,
                                                                                                          sst);
       __syncthreads();
-      adj_passes_smem<1, L, false, LINES, false, NP - 1, 1>(sm, tw);
+      adj_passes_smem<1, L, false, LINES, false, LS, NP - 1, 1>(sm, tw);
       stockham_pass<1, true, L, radix_at(L, false, 0), 1, LINES, false, false>(tw, sld, gst);
     }
   }
@@ -458,10 +644,10 @@ __global__ void __launch_bounds__(3 * zconv_cols(L) * L / GBD_E, min_blocks(3 * 
   } else {
     stockham_pass<-1, false, L, radix_at(L, true, 0), 1, LINES, true, false>(tw, gld, sst);
     __syncthreads();
-    fwd_passes_smem<-1, L, true, LINES, true, 1, NP - 1>(sm, tw);
+    fwd_passes_smem<-1, L, true, LINES, true, LS, 1, NP - 1>(sm, tw);
     run_fused(sld, sst);
     __syncthreads();
-    adj_passes_smem<1, L, true, LINES, true, NP - 1, 1>(sm, tw);
+    adj_passes_smem<1, L, true, LINES, true, LS, NP - 1, 1>(sm, tw);
     stockham_pass<1, true, L, radix_at(L, true, 0), 1, LINES, true, false>(tw, sld, gst);
   }
 }
@@ -486,7 +672,7 @@ template <int LX>
 static void row_launch_t(const RowArgs& a, const float2* tw, cudaStream_t st) {
   constexpr int RB = row_rb(LX);
   constexpr int T = 3 * RB * LX / GBD_E;
-  const size_t smem = (size_t)3 * RB * line_stride<LX, false>() * sizeof(float2);
+  const size_t smem = (size_t)3 * RB * line_stride<LX, true>() * sizeof(float2);
   prep(row_kernel<LX>, smem);
   row_kernel<LX><<<(a.rows + RB - 1) / RB, T, smem, st>>>(a, tw);
 }
