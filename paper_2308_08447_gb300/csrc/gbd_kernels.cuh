@@ -17,7 +17,7 @@ enum RowMode : int {
 };
 
 // Block shapes, shared by host planning and the kernels (L = transform length).
-__host__ __device__ constexpr int row_rb(int Lx) { return Lx >= 2048 ? 1 : 2048 / Lx; }  // rows per block
+__host__ __device__ constexpr int row_rb(int Lx) { return Lx >= 4096 ? 1 : 4096 / Lx; }  // rows per block
 __host__ __device__ constexpr int film_cols(int Py) { return Py >= 1024 ? 1 : 1024 / Py; }
 __host__ __device__ constexpr int ypass_lines(int Py) { return Py >= 4096 ? 1 : 4096 / Py; }
 __host__ __device__ constexpr int zconv_cols(int Pz) { return Pz >= 2048 ? 1 : 2048 / Pz; }
