@@ -96,6 +96,33 @@ gbd_status gbd_llg_rhs(gbd_mesh* mesh, const float* m, float* dmdt, void* stream
  * each step. m: device [3][nz][ny][nx] float32 unit vectors. nsteps = 0 is a no-op. */
 gbd_status gbd_llg_step(gbd_mesh* mesh, float* m, int nsteps, double dt, void* stream);
 
+/* ---- allocation-free demag --------------------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that cannot call
+ * cudaMalloc at the moment they need the field -- for example code embedded in a host
+ * application that owns every device allocation through its own pool, or code at a memory
+ * cap where an allocation (and the device synchronisation it can imply) is not acceptable.
+ *
+ * gbd_demag_noalloc computes exactly what gbd_demag computes, H = H_d(M), with the same
+ * kernels, but its scratch (the x spectrum and, for 3D meshes, the y spectrum) lives in a
+ * fixed device array compiled into the library instead of the mesh's buffers, and the call
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine). The mesh still
+ * supplies its kernel spectrum and twiddle table (set up earlier by gbd_mesh_create and
+ * gbd_set_kernel); M and H are the caller's, as for gbd_demag.
+ *   - Limit: the scratch needed, x spectrum (3*nz*(Px/2+1)*ny complex64, rounded up to 256
+ *     bytes) plus y spectrum (3*nz*(Px/2+1)*Py complex64 when nz > 1 and ny > 1), must not
+ *     exceed GBD_NOALLOC_MAX_BYTES; a larger mesh is refused with GBD_EBUDGET before any
+ *     work is enqueued. Every GPU that loads the library holds this array until exit.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ *     with that device current) and caches it; make that first call before any stream
+ *     capture.
+ *   - All calls on a device share the one array, which keeps the last call's contents. Each
+ *     call writes every scratch element before reading it, so nothing needs clearing; but
+ *     calls whose work overlaps on the GPU (different streams, other meshes) race on it and
+ *     must be ordered by the caller.
+ * Errors: as gbd_demag, plus GBD_EBUDGET (mesh too large for the static scratch). */
+#define GBD_NOALLOC_MAX_BYTES (64u << 20)
+gbd_status gbd_demag_noalloc(gbd_mesh* mesh, const float* M, float* H, void* stream);
+
 /* Frees the mesh's device buffers (after synchronizing the device). NULL is accepted. */
 gbd_status gbd_mesh_destroy(gbd_mesh* mesh);
 

@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -491,3 +492,90 @@ gbd_status gbd_llg_step(gbd_mesh* m, float* mm, int nsteps, double dt, void* str
 }
 
 }  // extern "C"
+
+// ---- allocation-free demag -------------------------------------------------------------------
+//
+// Scratch for gbd_demag_noalloc: the x spectrum and, for 3D meshes, the y spectrum of one
+// demag evaluation live in this file-scope device array instead of the mesh's buffers.
+// Every GPU that loads the library holds it (GBD_NOALLOC_MAX_BYTES) until the process exits.
+// Host code cannot use the symbol as a device address: its device address is looked up once
+// per device with cudaGetSymbolAddress, with that device current, and passed to the kernels.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GBD_NOALLOC_MAX_BYTES];
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoallocMaxDevices] = {nullptr};
+
+// Same pass sequence as enqueue_conv, on caller-chosen spectrum buffers.
+void enqueue_conv_on(const gbd_mesh* m, float2* S, float2* T, cudaStream_t st) {
+  const gbd::Plan& p = m->p;
+  gbd::ColArgs a = col_args(m);
+  if (p.film) {
+    a.dst = S;
+    a.Kf = static_cast<const float4*>(m->K);
+    gbd::launch_film_conv(a, m->tw, st);
+    return;
+  }
+  a.K3 = static_cast<const float*>(m->K);
+  if (p.ny > 1) {
+    a.lines_total = 3LL * p.nz * p.Hx;
+    a.src = S;
+    a.dst = T;
+    gbd::launch_y_fwd(a, m->tw, st);
+    a.Q = (long long)p.Hx * p.Py;
+    a.Pyq = p.Py;
+    gbd::launch_z_conv(a, m->tw, st);
+    a.src = T;
+    a.dst = S;
+    gbd::launch_y_inv(a, m->tw, st);
+  } else {
+    a.dst = S;
+    a.Q = p.Hx;
+    a.Pyq = 1;
+    gbd::launch_z_conv(a, m->tw, st);
+  }
+}
+}  // namespace
+
+extern "C" gbd_status gbd_demag_noalloc(gbd_mesh* m, const float* M, float* H, void* stream) {
+  gbd_status s = ready(m);
+  if (s != GBD_OK) return s;
+  if (!ptr_ok(M) || !ptr_ok(H)) return fail(GBD_EINVAL, "M and H must be non-NULL, 4-byte aligned device pointers");
+  const gbd::Plan& p = m->p;
+  const size_t s_bytes = (p.bytes_S + 255) / 256 * 256;
+  const size_t need = s_bytes + p.bytes_T;
+  if (need > (size_t)GBD_NOALLOC_MAX_BYTES)
+    return fail(GBD_EBUDGET, "gbd_demag_noalloc: this mesh needs " + std::to_string(need) +
+                                 " bytes of scratch, more than the static maximum of " +
+                                 std::to_string((size_t)GBD_NOALLOC_MAX_BYTES));
+  int dev = m->device;
+  if (dev < 0 || dev >= kNoallocMaxDevices) return fail(GBD_EUNSUPPORTED, "gbd_demag_noalloc: device ordinal out of range");
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* ptr = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess || !ptr) return cuda_fail(e, "gbd_demag_noalloc: cudaGetSymbolAddress");
+      g_noalloc_addr[dev] = ptr;
+    }
+    base = g_noalloc_addr[dev];
+  }
+  float2* S = static_cast<float2*>(base);
+  float2* T = p.bytes_T ? reinterpret_cast<float2*>(static_cast<unsigned char*>(base) + s_bytes) : nullptr;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  gbd::RowArgs a = row_args(m);
+  a.S = S;
+  a.in = M;
+  a.mode = gbd::ROW_FWD;
+  a.fwd_after = 1;
+  gbd::launch_row(p.Lx, a, m->tw, st);
+  enqueue_conv_on(m, S, T, st);
+  a.hscale = 1.f;
+  a.out = H;
+  a.mode = gbd::ROW_H;
+  a.fwd_after = 0;
+  gbd::launch_row(p.Lx, a, m->tw, st);
+  return after_launch("gbd_demag_noalloc");
+}

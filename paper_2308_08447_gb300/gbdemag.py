@@ -51,6 +51,7 @@ _SIG = {
     "gbd_tensor_at": [ctypes.POINTER(gbd_mesh_desc), _I, _I, _I, ctypes.POINTER(_D)],
     "gbd_plan_dims": [ctypes.POINTER(gbd_mesh_desc), ctypes.POINTER(_I)],
     "gbd_kernel_spectrum_host": [ctypes.POINTER(gbd_mesh_desc), ctypes.POINTER(_D), ctypes.c_size_t],
+    "gbd_demag_noalloc": [_P, _P, _P, _P],
     "gbd_mesh_set_timing": [_P, _I],
     "gbd_mesh_read_timing": [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)],
 }
@@ -138,6 +139,13 @@ def gbd_set_kernel(mesh, stream=None):
 
 def gbd_demag(mesh, M, H, shape, stream=None):
     _check(load().gbd_demag(mesh, _field_ptr(M, shape, "M"), _field_ptr(H, shape, "H"), _stream_ptr(stream)))
+
+
+def gbd_demag_noalloc(mesh, M, H, shape, stream=None):
+    """H = H_d(M) like gbd_demag, with the scratch in the library's static device array
+    (no allocation in the call; see include/gbdemag.h for the size limit and ordering)."""
+    _check(load().gbd_demag_noalloc(mesh, _field_ptr(M, shape, "M"), _field_ptr(H, shape, "H"),
+                                    _stream_ptr(stream)))
 
 
 def gbd_effective_field(mesh, m, H, shape, stream=None):
