@@ -130,7 +130,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("gbd_fft.cuh", "gbd_kernels.cu", "gbd_kernels.cuh"):
+    for f in ("gbd_fft.cuh", "gbd_kernels.cuh", "gbd_launch.cuh", "gbd_row.cu", "gbd_conv.cu", "gbd_ypass.cu"):
         with open(os.path.join(ROOT, "paper_2308_08447_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

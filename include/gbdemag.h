@@ -129,6 +129,40 @@ gbd_status gbd_mesh_destroy(gbd_mesh* mesh);
 /* Message of the calling thread's last failure ("" if none). Valid until its next call. */
 const char* gbd_last_error(void);
 
+/* ---- tile-shape autotuning ---------------------------------------------------------------
+ * Every kernel family has two tile shapes (lines of the transform per thread block). They
+ * give identical results -- each line's FFT and each cell's update do not depend on how lines
+ * are grouped -- and differ only in speed, which depends on the mesh size. gbd_mesh_autotune
+ * times both shapes of each pass this mesh uses (on its own buffers, which it zeroes; the
+ * stream is synchronized) and keeps the faster; results are cached per (nx, ny, nz, device)
+ * in the process and, when the environment variable GBD_AUTOTUNE_CACHE names a file, in that
+ * text file. Requires gbd_set_kernel. Variants (row, film, y, z) are each 0 or 1. */
+gbd_status gbd_mesh_autotune(gbd_mesh* mesh, void* stream);
+gbd_status gbd_mesh_get_tuning(const gbd_mesh* mesh, int out[4]);
+gbd_status gbd_mesh_set_tuning(gbd_mesh* mesh, const int in[4]);
+
+/* ---- batched meshes ------------------------------------------------------------------------
+ * A batch advances many independent meshes (uneven sizes allowed) with one CUDA-graph launch
+ * per run: each mesh's gbd_llg_step launch sequence is a chain on one of up to 32 branch
+ * streams, captured into one graph behind a fork on `stream` and joined back into it, so
+ * kernels of different meshes run concurrently. The instantiated graph is cached with the
+ * run's arguments and relaunched while they repeat. Each mesh's result is bit-identical to
+ * gbd_llg_step on that mesh alone. */
+typedef struct gbd_batch gbd_batch;
+
+/* meshes: count >= 1 distinct meshes on the current device, each after gbd_set_kernel; the
+ * batch keeps the pointers (the meshes must outlive it). */
+gbd_status gbd_batch_create(gbd_mesh* const* meshes, int count, gbd_batch** out);
+
+/* Advances mesh i's state m[i] (device, [3][nz][ny][nx] unit vectors, in place) by nsteps[i]
+ * RK4 steps of size dt[i] (nsteps[i] = 0 leaves it untouched). Enqueue-only on `stream`. Two
+ * runs of one batch must not overlap on the GPU (they share the meshes' scratch).
+ * Errors: GBD_EINVAL (NULL / misaligned pointer, nsteps < 0, dt <= 0), GBD_ECUDA. */
+gbd_status gbd_batch_run(gbd_batch* batch, float* const* m, const int* nsteps, const double* dt, void* stream);
+
+/* Synchronizes the device and frees the batch (not the meshes). NULL is accepted. */
+gbd_status gbd_batch_destroy(gbd_batch* batch);
+
 /* ---- per-pass timing ------------------------------------------------------------------- */
 
 /* Pass classes reported by gbd_mesh_read_timing. */

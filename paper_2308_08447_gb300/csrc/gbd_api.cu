@@ -1,10 +1,13 @@
 // C ABI of the demag convolution + exchange/LLG/RK4 library (declarations and contracts in
 // include/gbdemag.h). Host side: argument checks, planning, device buffers, the kernel
 // spectrum upload and the launch sequences of Eq. 1 (Sec. II) and of the RK4 time step.
+#include <array>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -102,10 +105,10 @@ bool make_plan(int nx, int ny, int nz, Plan& p, const char** why) {
   p.Kz = p.Pz / 2 + 1;
   p.film = (nz == 1);
   // block shapes (the kernels are compiled for these per transform length)
-  p.RB = row_rb(p.Lx);
-  p.Cf = film_cols(p.Py);
-  p.Cy = ypass_lines(p.Py);
-  p.Wz = zconv_cols(p.Pz);
+  p.RB = row_rb(p.Lx, p.var_row);
+  p.Cf = film_cols(p.Py, p.var_film);
+  p.Cy = ypass_lines(p.Py, p.var_y);
+  p.Wz = zconv_cols(p.Pz, p.var_z);
   p.bytes_S = (size_t)3 * nz * p.Hx * ny * sizeof(float2);
   p.bytes_T = (!p.film && ny > 1) ? (size_t)3 * nz * p.Hx * p.Py * sizeof(float2) : 0;
   p.bytes_K = p.film ? (size_t)p.Hx * p.Ky * sizeof(float4) : (size_t)p.Hx * p.Ky * p.Kz * 6 * sizeof(float);
@@ -206,7 +209,7 @@ static void enqueue_conv(gbd_mesh* m, cudaStream_t st) {
   if (p.film) {
     a.dst = m->S;
     a.Kf = static_cast<const float4*>(m->K);
-    timed(m, GBD_PASS_FILM_CONV, st, [&] { gbd::launch_film_conv(a, m->tw, st); });
+    timed(m, GBD_PASS_FILM_CONV, st, [&] { gbd::launch_film_conv(m->p.var_film, a, m->tw, st); });
     return;
   }
   a.K3 = static_cast<const float*>(m->K);
@@ -214,19 +217,19 @@ static void enqueue_conv(gbd_mesh* m, cudaStream_t st) {
     a.lines_total = 3LL * p.nz * p.Hx;
     a.src = m->S;
     a.dst = m->T;
-    timed(m, GBD_PASS_Y_FWD, st, [&] { gbd::launch_y_fwd(a, m->tw, st); });
+    timed(m, GBD_PASS_Y_FWD, st, [&] { gbd::launch_y_fwd(m->p.var_y, a, m->tw, st); });
     a.dst = m->T;
     a.Q = (long long)p.Hx * p.Py;
     a.Pyq = p.Py;
-    timed(m, GBD_PASS_Z_CONV, st, [&] { gbd::launch_z_conv(a, m->tw, st); });
+    timed(m, GBD_PASS_Z_CONV, st, [&] { gbd::launch_z_conv(m->p.var_z, a, m->tw, st); });
     a.src = m->T;
     a.dst = m->S;
-    timed(m, GBD_PASS_Y_INV, st, [&] { gbd::launch_y_inv(a, m->tw, st); });
+    timed(m, GBD_PASS_Y_INV, st, [&] { gbd::launch_y_inv(m->p.var_y, a, m->tw, st); });
   } else {
     a.dst = m->S;
     a.Q = p.Hx;
     a.Pyq = 1;
-    timed(m, GBD_PASS_Z_CONV, st, [&] { gbd::launch_z_conv(a, m->tw, st); });
+    timed(m, GBD_PASS_Z_CONV, st, [&] { gbd::launch_z_conv(m->p.var_z, a, m->tw, st); });
   }
 }
 
@@ -329,6 +332,21 @@ gbd_status gbd_mesh_create(const gbd_mesh_desc* desc, gbd_mesh** out) {
     delete m;
     return cuda_fail(e, "cudaMemcpy twiddles");
   }
+  // shared-memory attributes of this mesh's kernels (both tile variants), set now so that
+  // later launches, also inside a stream capture, need no configuration call
+  gbd::prepare_row(p.Lx);
+  if (p.film) {
+    gbd::prepare_film_conv(p.Py);
+  } else {
+    gbd::prepare_z_conv(p.Pz);
+    if (p.ny > 1) gbd::prepare_y_passes(p.Py);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    free_mesh_buffers(m);
+    delete m;
+    return cuda_fail(e, "kernel attributes");
+  }
   *out = m;
   return GBD_OK;
 }
@@ -420,13 +438,13 @@ gbd_status gbd_demag(gbd_mesh* m, const float* M, float* H, void* stream) {
   a.in = M;
   a.mode = gbd::ROW_FWD;
   a.fwd_after = 1;
-  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, a, m->tw, st); });
+  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, a, m->tw, st); });
   enqueue_conv(m, st);
   a.hscale = 1.f;
   a.out = H;
   a.mode = gbd::ROW_H;
   a.fwd_after = 0;
-  timed(m, GBD_PASS_ROW_INV, st, [&] { gbd::launch_row(m->p.Lx, a, m->tw, st); });
+  timed(m, GBD_PASS_ROW_INV, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, a, m->tw, st); });
   return after_launch("gbd_demag");
 }
 
@@ -439,13 +457,13 @@ static gbd_status field_like(gbd_mesh* m, const float* mm, float* out, int mode,
   a.in = mm;
   a.mode = gbd::ROW_FWD;
   a.fwd_after = 1;
-  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, a, m->tw, st); });
+  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, a, m->tw, st); });
   enqueue_conv(m, st);
   a.ms = mm;
   a.out = out;
   a.mode = mode;
   a.fwd_after = 0;
-  timed(m, GBD_PASS_ROW_INV, st, [&] { gbd::launch_row(m->p.Lx, a, m->tw, st); });
+  timed(m, GBD_PASS_ROW_INV, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, a, m->tw, st); });
   return after_launch(name);
 }
 
@@ -470,7 +488,7 @@ gbd_status gbd_llg_step(gbd_mesh* m, float* mm, int nsteps, double dt, void* str
   a.in = mm;
   a.mode = gbd::ROW_FWD;
   a.fwd_after = 1;
-  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, a, m->tw, st); });
+  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, a, m->tw, st); });
   a.m0 = mm;
   a.m0_out = mm;
   a.acc = m->acc;
@@ -485,7 +503,7 @@ gbd_status gbd_llg_step(gbd_mesh* m, float* mm, int nsteps, double dt, void* str
       a.mnext = mn[stage];
       a.mode = gbd::ROW_RK1 + stage;
       a.fwd_after = (last && stage == 3) ? 0 : 1;
-      timed(m, GBD_PASS_ROW_RK, st, [&] { gbd::launch_row(m->p.Lx, a, m->tw, st); });
+      timed(m, GBD_PASS_ROW_RK, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, a, m->tw, st); });
     }
   }
   return after_launch("gbd_llg_step");
@@ -514,7 +532,7 @@ void enqueue_conv_on(const gbd_mesh* m, float2* S, float2* T, cudaStream_t st) {
   if (p.film) {
     a.dst = S;
     a.Kf = static_cast<const float4*>(m->K);
-    gbd::launch_film_conv(a, m->tw, st);
+    gbd::launch_film_conv(m->p.var_film, a, m->tw, st);
     return;
   }
   a.K3 = static_cast<const float*>(m->K);
@@ -522,18 +540,18 @@ void enqueue_conv_on(const gbd_mesh* m, float2* S, float2* T, cudaStream_t st) {
     a.lines_total = 3LL * p.nz * p.Hx;
     a.src = S;
     a.dst = T;
-    gbd::launch_y_fwd(a, m->tw, st);
+    gbd::launch_y_fwd(m->p.var_y, a, m->tw, st);
     a.Q = (long long)p.Hx * p.Py;
     a.Pyq = p.Py;
-    gbd::launch_z_conv(a, m->tw, st);
+    gbd::launch_z_conv(m->p.var_z, a, m->tw, st);
     a.src = T;
     a.dst = S;
-    gbd::launch_y_inv(a, m->tw, st);
+    gbd::launch_y_inv(m->p.var_y, a, m->tw, st);
   } else {
     a.dst = S;
     a.Q = p.Hx;
     a.Pyq = 1;
-    gbd::launch_z_conv(a, m->tw, st);
+    gbd::launch_z_conv(m->p.var_z, a, m->tw, st);
   }
 }
 }  // namespace
@@ -570,12 +588,378 @@ extern "C" gbd_status gbd_demag_noalloc(gbd_mesh* m, const float* M, float* H, v
   a.in = M;
   a.mode = gbd::ROW_FWD;
   a.fwd_after = 1;
-  gbd::launch_row(p.Lx, a, m->tw, st);
+  gbd::launch_row(p.Lx, p.var_row, a, m->tw, st);
   enqueue_conv_on(m, S, T, st);
   a.hscale = 1.f;
   a.out = H;
   a.mode = gbd::ROW_H;
   a.fwd_after = 0;
-  gbd::launch_row(p.Lx, a, m->tw, st);
+  gbd::launch_row(p.Lx, p.var_row, a, m->tw, st);
   return after_launch("gbd_demag_noalloc");
+}
+
+// ---- tile-shape autotuner --------------------------------------------------------------------
+//
+// Each kernel family has two tile shapes (lines per block; gbd_kernels.cuh). They compute the
+// same numbers -- every line's transform and every cell's update is independent of how lines
+// are grouped into blocks -- so the choice only changes speed. gbd_mesh_autotune times both
+// shapes of each pass the mesh uses, on the mesh's own (zeroed) buffers, keeps the faster one,
+// and caches the choice by mesh size and device: in the process, and in the text file named
+// by GBD_AUTOTUNE_CACHE when that is set (lines "nx ny nz device var_row var_film var_y var_z").
+
+namespace {
+struct TuneKey {
+  int nx, ny, nz, dev;
+  bool operator<(const TuneKey& o) const {
+    if (nx != o.nx) return nx < o.nx;
+    if (ny != o.ny) return ny < o.ny;
+    if (nz != o.nz) return nz < o.nz;
+    return dev < o.dev;
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::array<int, 4>> g_tune;
+bool g_tune_file_read = false;
+
+const char* tune_file() {
+  const char* p = std::getenv("GBD_AUTOTUNE_CACHE");
+  return (p && *p) ? p : nullptr;
+}
+
+void read_tune_file_locked() {
+  if (g_tune_file_read) return;
+  g_tune_file_read = true;
+  const char* path = tune_file();
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  TuneKey k;
+  std::array<int, 4> v;
+  while (std::fscanf(f, "%d %d %d %d %d %d %d %d", &k.nx, &k.ny, &k.nz, &k.dev, &v[0], &v[1], &v[2], &v[3]) == 8) {
+    bool ok = true;
+    for (int x : v) ok = ok && (x == 0 || x == 1);
+    if (ok) g_tune[k] = v;
+  }
+  std::fclose(f);
+}
+
+void append_tune_file_locked(const TuneKey& k, const std::array<int, 4>& v) {
+  const char* path = tune_file();
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%d %d %d %d %d %d %d %d\n", k.nx, k.ny, k.nz, k.dev, v[0], v[1], v[2], v[3]);
+  std::fclose(f);
+}
+
+void apply_tuning(gbd_mesh* m, const std::array<int, 4>& v) {
+  gbd::Plan& p = m->p;
+  p.var_row = v[0];
+  p.var_film = v[1];
+  p.var_y = v[2];
+  p.var_z = v[3];
+  p.RB = gbd::row_rb(p.Lx, p.var_row);
+  p.Cf = gbd::film_cols(p.Py, p.var_film);
+  p.Cy = gbd::ypass_lines(p.Py, p.var_y);
+  p.Wz = gbd::zconv_cols(p.Pz, p.var_z);
+}
+
+// Mean device time in ms of one launch made by f(variant), over `reps` launches after one
+// untimed launch.
+template <class F>
+cudaError_t time_variant(cudaStream_t st, int reps, F f, float* ms) {
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return e;
+  }
+  f();
+  cudaEventRecord(e0, st);
+  for (int i = 0; i < reps; ++i) f();
+  cudaEventRecord(e1, st);
+  e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  *ms = t / reps;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e;
+}
+}  // namespace
+
+extern "C" gbd_status gbd_mesh_get_tuning(const gbd_mesh* m, int out[4]) {
+  if (!m || !out) return fail(GBD_EINVAL, "NULL argument");
+  out[0] = m->p.var_row;
+  out[1] = m->p.var_film;
+  out[2] = m->p.var_y;
+  out[3] = m->p.var_z;
+  return GBD_OK;
+}
+
+extern "C" gbd_status gbd_mesh_set_tuning(gbd_mesh* m, const int in[4]) {
+  if (!m || !in) return fail(GBD_EINVAL, "NULL argument");
+  std::array<int, 4> v;
+  for (int i = 0; i < 4; ++i) {
+    if (in[i] != 0 && in[i] != 1) return fail(GBD_EINVAL, "tile variants are 0 or 1");
+    v[i] = in[i];
+  }
+  apply_tuning(m, v);
+  return GBD_OK;
+}
+
+extern "C" gbd_status gbd_mesh_autotune(gbd_mesh* m, void* stream) {
+  gbd_status s = ready(m);
+  if (s != GBD_OK) return s;
+  const gbd::Plan& p = m->p;
+  const TuneKey key{p.nx, p.ny, p.nz, m->device};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    read_tune_file_locked();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      apply_tuning(m, it->second);
+      return GBD_OK;
+    }
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // zeroed buffers keep every timed pass finite
+  cudaError_t e = cudaSuccess;
+  if (p.bytes_S) e = cudaMemsetAsync(m->S, 0, p.bytes_S, st);
+  if (e == cudaSuccess && p.bytes_T) e = cudaMemsetAsync(m->T, 0, p.bytes_T, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->acc, 0, p.bytes_state / 3, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->bufA, 0, p.bytes_state / 3, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->bufB, 0, p.bytes_state / 3, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gbd_mesh_autotune: memset");
+  const int reps = 5;
+  std::array<int, 4> best = {p.var_row, p.var_film, p.var_y, p.var_z};
+  auto pick = [&](int slot, auto launch_v) -> cudaError_t {
+    float t[2];
+    for (int v = 0; v < 2; ++v) {
+      cudaError_t ee = time_variant(st, reps, [&] { launch_v(v); }, &t[v]);
+      if (ee != cudaSuccess) return ee;
+    }
+    // keep the default unless the other shape is faster by more than 2 %
+    const int def = best[slot];
+    best[slot] = (t[1 - def] < 0.98f * t[def]) ? 1 - def : def;
+    return cudaSuccess;
+  };
+  // x rows: an RK4 middle stage with the next forward transform, on zeroed state
+  gbd::RowArgs ra = row_args(m);
+  ra.dt = 1e-13f;
+  ra.ms = m->bufA;
+  ra.m0 = m->bufB;
+  ra.mnext = m->bufB;
+  ra.acc = m->acc;
+  ra.mode = gbd::ROW_RK2;
+  ra.fwd_after = 1;
+  e = pick(0, [&](int v) { gbd::launch_row(p.Lx, v, ra, m->tw, st); });
+  gbd::ColArgs ca = col_args(m);
+  if (e == cudaSuccess && p.film) {
+    ca.dst = m->S;
+    ca.Kf = static_cast<const float4*>(m->K);
+    e = pick(1, [&](int v) { gbd::launch_film_conv(v, ca, m->tw, st); });
+  } else if (e == cudaSuccess) {
+    ca.K3 = static_cast<const float*>(m->K);
+    if (p.ny > 1) {
+      ca.lines_total = 3LL * p.nz * p.Hx;
+      ca.src = m->S;
+      ca.dst = m->T;
+      e = pick(2, [&](int v) {
+        gbd::launch_y_fwd(v, ca, m->tw, st);
+        gbd::ColArgs cb = ca;
+        cb.src = m->T;
+        cb.dst = m->S;
+        gbd::launch_y_inv(v, cb, m->tw, st);
+      });
+      ca.dst = m->T;
+      ca.Q = (long long)p.Hx * p.Py;
+      ca.Pyq = p.Py;
+    } else {
+      ca.dst = m->S;
+      ca.Q = p.Hx;
+      ca.Pyq = 1;
+    }
+    if (e == cudaSuccess) e = pick(3, [&](int v) { gbd::launch_z_conv(v, ca, m->tw, st); });
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "gbd_mesh_autotune");
+  apply_tuning(m, best);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (g_tune.find(key) == g_tune.end()) {
+    g_tune[key] = best;
+    append_tune_file_locked(key, best);
+  }
+  return GBD_OK;
+}
+
+// ---- batched meshes: one CUDA graph per run ------------------------------------------------
+//
+// A batch advances many independent meshes. Each mesh's launch sequence (the same as
+// gbd_llg_step's) is a chain on one of up to kBatchBranches branch streams; the chains are
+// captured into one CUDA graph behind a fork event and joined back into the caller's stream,
+// so the GPU runs kernels of different meshes side by side and the host makes one graph
+// launch per run. The instantiated graph is cached with its arguments (state pointers,
+// step counts, time steps) and relaunched while they repeat.
+
+struct gbd_batch {
+  std::vector<gbd_mesh*> meshes;
+  int device = -1;
+  cudaStream_t origin = nullptr;  // capture and launch stream (the legacy default stream cannot be captured)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<cudaStream_t> branches;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  std::vector<float*> key_m;
+  std::vector<int> key_steps;
+  std::vector<double> key_dt;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+constexpr int kBatchBranches = 32;
+
+// gbd_llg_step's launch sequence for one mesh on one stream (no timing events).
+void enqueue_llg(gbd_mesh* m, float* mm, int nsteps, double dt, cudaStream_t st) {
+  if (nsteps <= 0) return;
+  gbd::RowArgs a = row_args(m);
+  a.dt = (float)dt;
+  a.in = mm;
+  a.mode = gbd::ROW_FWD;
+  a.fwd_after = 1;
+  gbd::launch_row(m->p.Lx, m->p.var_row, a, m->tw, st);
+  a.m0 = mm;
+  a.m0_out = mm;
+  a.acc = m->acc;
+  for (int step = 0; step < nsteps; ++step) {
+    const bool last = (step == nsteps - 1);
+    const float* ms[4] = {mm, m->bufA, m->bufB, m->bufA};
+    float* mn[4] = {m->bufA, m->bufB, m->bufA, nullptr};
+    for (int stage = 0; stage < 4; ++stage) {
+      const bool tmp = m->timing;
+      m->timing = false;
+      enqueue_conv(m, st);
+      m->timing = tmp;
+      a.ms = ms[stage];
+      a.mnext = mn[stage];
+      a.mode = gbd::ROW_RK1 + stage;
+      a.fwd_after = (last && stage == 3) ? 0 : 1;
+      gbd::launch_row(m->p.Lx, m->p.var_row, a, m->tw, st);
+    }
+  }
+}
+
+void destroy_batch(gbd_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (cudaStream_t s : b->branches) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  delete b;
+}
+}  // namespace
+
+extern "C" gbd_status gbd_batch_create(gbd_mesh* const* meshes, int count, gbd_batch** out) {
+  if (!out) return fail(GBD_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!meshes || count < 1) return fail(GBD_EINVAL, "meshes must be a non-empty array");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  for (int i = 0; i < count; ++i) {
+    if (!meshes[i]) return fail(GBD_EINVAL, "meshes[" + std::to_string(i) + "] is NULL");
+    if (!meshes[i]->kernel_set) return fail(GBD_ESTATE, "gbd_set_kernel has not been called on meshes[" + std::to_string(i) + "]");
+    if (meshes[i]->device != dev) return fail(GBD_EINVAL, "all meshes must live on the current device");
+    for (int j = 0; j < i; ++j)
+      if (meshes[j] == meshes[i]) return fail(GBD_EINVAL, "a mesh appears twice in the batch");
+  }
+  gbd_batch* b = new (std::nothrow) gbd_batch();
+  if (!b) return fail(GBD_ENOMEM, "host allocation failed");
+  b->meshes.assign(meshes, meshes + count);
+  b->device = dev;
+  const int nb = count < kBatchBranches ? count : kBatchBranches;
+  e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+  for (int i = 0; i < nb && e == cudaSuccess; ++i) {
+    cudaStream_t s;
+    cudaEvent_t j;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) break;
+    b->branches.push_back(s);
+    e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+    if (e != cudaSuccess) break;
+    b->join.push_back(j);
+  }
+  if (e != cudaSuccess) {
+    destroy_batch(b);
+    return cuda_fail(e, "gbd_batch_create");
+  }
+  *out = b;
+  return GBD_OK;
+}
+
+extern "C" gbd_status gbd_batch_run(gbd_batch* b, float* const* m, const int* nsteps, const double* dt, void* stream) {
+  if (!b || !m || !nsteps || !dt) return fail(GBD_EINVAL, "NULL argument");
+  const int n = (int)b->meshes.size();
+  for (int i = 0; i < n; ++i) {
+    if (!ptr_ok(m[i])) return fail(GBD_EINVAL, "m[" + std::to_string(i) + "] must be a non-NULL, 4-byte aligned device pointer");
+    if (nsteps[i] < 0) return fail(GBD_EINVAL, "nsteps must be >= 0");
+    if (!(dt[i] > 0) || !std::isfinite(dt[i])) return fail(GBD_EINVAL, "dt must be finite and > 0");
+  }
+  gbd_status s = check_device(b->meshes[0]);
+  if (s != GBD_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaStream_t og = b->origin;
+  const bool same = b->exec && b->key_m == std::vector<float*>(m, m + n) &&
+                    b->key_steps == std::vector<int>(nsteps, nsteps + n) &&
+                    b->key_dt == std::vector<double>(dt, dt + n);
+  if (!same) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(og, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "gbd_batch_run: begin capture");
+    cudaEventRecord(b->fork, og);
+    const int nb = (int)b->branches.size();
+    for (int j = 0; j < nb; ++j) cudaStreamWaitEvent(b->branches[j], b->fork, 0);
+    for (int i = 0; i < n; ++i) enqueue_llg(b->meshes[i], m[i], nsteps[i], dt[i], b->branches[i % nb]);
+    for (int j = 0; j < nb; ++j) {
+      cudaEventRecord(b->join[j], b->branches[j]);
+      cudaStreamWaitEvent(og, b->join[j], 0);
+    }
+    e = cudaStreamEndCapture(og, &graph);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      b->exec = nullptr;
+      cudaGetLastError();
+      return cuda_fail(e, "gbd_batch_run: graph capture");
+    }
+    b->key_m.assign(m, m + n);
+    b->key_steps.assign(nsteps, nsteps + n);
+    b->key_dt.assign(dt, dt + n);
+  }
+  // order the graph after the caller's earlier work on `stream`, and later work after it
+  cudaEventRecord(b->ev_in, st);
+  cudaStreamWaitEvent(og, b->ev_in, 0);
+  cudaError_t e = cudaGraphLaunch(b->exec, og);
+  if (e != cudaSuccess) return cuda_fail(e, "gbd_batch_run: graph launch");
+  cudaEventRecord(b->ev_out, og);
+  cudaStreamWaitEvent(st, b->ev_out, 0);
+  return after_launch("gbd_batch_run");
+}
+
+extern "C" gbd_status gbd_batch_destroy(gbd_batch* b) {
+  if (!b) return GBD_OK;
+  if (b->device >= 0) cudaDeviceSynchronize();
+  destroy_batch(b);
+  return GBD_OK;
 }

@@ -1,4 +1,18 @@
-// Kernel argument blocks, block shapes and launch helpers for the demag / LLG passes.
+// Kernel argument blocks, block shapes and launchers of the demag / LLG passes.
+//
+// Passes of one demag evaluation (Sec. II, Eq. 1; the single-GPU steps of Appendix A), with
+// P the padded lengths, Lx = Px / 2, Hx = Lx + 1:
+//   row kernel, forward:  x real-to-complex of the zero-padded rows -> S [3][nz][Hx][ny]
+//   film (nz = 1):        film_conv: y FFT -> kernel product -> y IFFT, in place on S
+//   3D:                   y_fwd S -> T [3][nz][Hx][Py]; z_conv on T (z FFT -> product ->
+//                         z IFFT, only the nz stored planes); y_inv T -> S
+//   row kernel, inverse:  x complex-to-real + crop, then the mode's epilogue (field, dm/dt,
+//                         or exchange + LLG + RK4 stage followed by the next stage's forward
+//                         x transform, Sec. III).
+// The padding is never stored: loads past n_d read zeros and cropped outputs are not
+// written, so S keeps ny rows and T keeps nz planes. Every transform length is a template
+// parameter; the launchers dispatch on it and on a tile-shape variant (0 or 1) that the
+// autotuner picks per mesh.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -16,11 +30,24 @@ enum RowMode : int {
   ROW_RK4 = 7,
 };
 
-// Block shapes, shared by host planning and the kernels (L = transform length).
-__host__ __device__ constexpr int row_rb(int Lx) { return Lx >= 4096 ? 1 : 4096 / Lx; }  // rows per block
-__host__ __device__ constexpr int film_cols(int Py) { return Py >= 1024 ? 1 : 1024 / Py; }
-__host__ __device__ constexpr int ypass_lines(int Py) { return Py >= 4096 ? 1 : 4096 / Py; }
-__host__ __device__ constexpr int zconv_cols(int Pz) { return Pz >= 2048 ? 1 : 2048 / Pz; }
+// Block shapes per transform length L and tile variant v, shared by host planning and the
+// kernels. Every kernel has 16 complex values per thread, so threads = lines * L / 16.
+// rows per x-row block (3 lines each): 2048 or 4096 complex values per component
+__host__ __device__ constexpr int row_rb(int Lx, int v) {
+  return v == 0 ? (Lx >= 2048 ? 1 : 2048 / Lx) : (Lx >= 4096 ? 1 : 4096 / Lx);
+}
+// kx columns per film-convolution block (3 lines each)
+__host__ __device__ constexpr int film_cols(int Py, int v) {
+  return v == 0 ? (Py >= 1024 ? 1 : 1024 / Py) : (Py >= 4096 ? 1 : 2 * (Py >= 1024 ? 1 : 1024 / Py));
+}
+// y lines per 3D y-pass block
+__host__ __device__ constexpr int ypass_lines(int Py, int v) {
+  return v == 0 ? (Py >= 4096 ? 1 : 4096 / Py) : (Py >= 2048 ? 1 : 2048 / Py);
+}
+// (kx, ky) columns per z-convolution block (3 lines each)
+__host__ __device__ constexpr int zconv_cols(int Pz, int v) {
+  return v == 0 ? (Pz >= 2048 ? 1 : 2048 / Pz) : (Pz >= 1024 ? 1 : 1024 / Pz);
+}
 
 struct RowArgs {
   int nx, ny, nz;           // mesh
@@ -53,12 +80,20 @@ struct ColArgs {
   int Pyq;                  // y extent of the column index q (Py, or 1 when ny == 1)
 };
 
-// Launchers dispatch on the transform length (a power of two); they return false for a
-// length without an instantiation.
-bool launch_row(int Lx, const RowArgs& a, const float2* tw, cudaStream_t st);
-bool launch_film_conv(const ColArgs& a, const float2* tw, cudaStream_t st);
-bool launch_y_fwd(const ColArgs& a, const float2* tw, cudaStream_t st);
-bool launch_y_inv(const ColArgs& a, const float2* tw, cudaStream_t st);
-bool launch_z_conv(const ColArgs& a, const float2* tw, cudaStream_t st);
+// Launchers dispatch on the transform length (a power of two) and the tile variant; they
+// return false for a length without an instantiation.
+bool launch_row(int Lx, int var, const RowArgs& a, const float2* tw, cudaStream_t st);
+bool launch_film_conv(int var, const ColArgs& a, const float2* tw, cudaStream_t st);
+bool launch_y_fwd(int var, const ColArgs& a, const float2* tw, cudaStream_t st);
+bool launch_y_inv(int var, const ColArgs& a, const float2* tw, cudaStream_t st);
+bool launch_z_conv(int var, const ColArgs& a, const float2* tw, cudaStream_t st);
+
+// Set the kernels' shared-memory attribute for both variants of a length without launching
+// (done when a mesh is created, so later launches inside a stream capture need no driver
+// configuration call). Return false for a length without an instantiation.
+bool prepare_row(int Lx);
+bool prepare_film_conv(int Py);
+bool prepare_y_passes(int Py);
+bool prepare_z_conv(int Pz);
 
 }  // namespace gbd

@@ -20,7 +20,9 @@ struct Plan {
   int Lx = 0, Hx = 0;   // Lx = Px / 2, Hx = Lx + 1 stored x frequencies
   int Ky = 0, Kz = 0;   // stored y / z kernel frequencies: P/2 + 1 (1 when P = 1)
   bool film = false;    // nz == 1: 3-pass path
-  // block shapes
+  // tile variants (0 / 1) per kernel family, set by the autotuner, and the block shapes
+  // they give
+  int var_row = 1, var_film = 0, var_y = 0, var_z = 0;
   int RB = 1;           // rows per x-row block
   int Cf = 1;           // columns per film-conv block
   int Cy = 1;           // lines per y-pass block

@@ -1,22 +1,21 @@
-// sm_103a kernels of the demag convolution (Sec. II, Eq. 1; single-GPU steps of Appendix A)
-// and of the fused exchange (Eq. 4) + LLG (Eq. 5) + RK4 update (Sec. III).
-//
-// Passes of one demag evaluation (P = padded lengths, Lx = Px / 2, Hx = Lx + 1):
-//   row kernel, forward:  x real-to-complex of the zero-padded rows -> S [3][nz][Hx][ny]
-//   film (nz = 1):        film_conv: y FFT -> kernel product -> y IFFT, in place on S
-//   3D:                   y_fwd S -> T [3][nz][Hx][Py]; z_conv on T (z FFT -> product ->
-//                         z IFFT, only the nz stored planes); y_inv T -> S
-//   row kernel, inverse:  x complex-to-real + crop, then the mode's epilogue; the RK4
-//                         modes also run the next stage's forward x transform.
-// The padding is never stored: loads past n_d read zeros and cropped outputs are not
-// written, so S keeps ny rows and T keeps nz planes. Every transform length is a
-// template parameter; the host dispatches on it.
-#include "gbd_fft.cuh"
-#include "gbd_kernels.cuh"
+// sm_103a x-row kernel of the demag convolution (Sec. II, Eq. 1; the xFFT_R2C / xFFT_C2R
+// steps of Appendix A with one GPU) with the fused exchange (Eq. 4) + LLG (Eq. 5) + RK4
+// epilogue (Sec. III). The inverse x transform, the epilogue and the next stage's forward
+// x transform run in one launch on RB rows per block.
+#include <mutex>
+#include <set>
+#include <utility>
+
+#include "gbd_launch.cuh"
 
 namespace gbd {
 
-__host__ __device__ constexpr int min_blocks(int T) { return T >= 768 ? 1 : 768 / T; }
+bool prep_seen(const void* k, int dev) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> seen;
+  std::lock_guard<std::mutex> lock(mu);
+  return !seen.insert(std::make_pair(k, dev)).second;
+}
 
 // ---------------------------------------------------------------------------------------------
 // x rows: real-to-complex through a half-length complex FFT (Lx = Px / 2).
@@ -28,10 +27,10 @@ __host__ __device__ constexpr int min_blocks(int T) { return T >= 768 ? 1 : 768 
 // inverse, and the forward reads only those: the upper half is the zero padding.
 // ---------------------------------------------------------------------------------------------
 
-template <int LX>
-__global__ void __launch_bounds__(3 * row_rb(LX) * LX / GBD_E, min_blocks(3 * row_rb(LX) * LX / GBD_E))
+template <int LX, int RB_>
+__global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX / GBD_E))
     row_kernel(RowArgs a, const float2* __restrict__ tw) {
-  constexpr int RB = row_rb(LX);
+  constexpr int RB = RB_;
   constexpr int LINES = 3 * RB;
   constexpr int T = LINES * LX / GBD_E;
   constexpr int LS = line_stride<LX, true>();  // odd: the rows' lines fall on different banks
@@ -425,358 +424,48 @@ __global__ void __launch_bounds__(3 * row_rb(LX) * LX / GBD_E, min_blocks(3 * ro
   }
 }
 
-// ---------------------------------------------------------------------------------------------
-// Kernel product H~_a = sum_b K~_ab M~_b with the packed real spectrum. Stored indices are
-// k' = k for k <= P/2 and P - k above; components odd along that axis change sign there
-// (xy, yz odd in y; xz, yz odd in z). The 1/(Px Py Pz) and the minus sign of Eq. 1 are in K~.
-// The last forward pass, the product and the first adjoint pass run in registers on one
-// thread per butterfly position j, for all three components.
-// ---------------------------------------------------------------------------------------------
 
-template <int L, int RL, int NSL, class LD, class ST, class MUL>
-__device__ __forceinline__ void fused_item(int line0, int lstride, int j, const float2* __restrict__ tw, LD ld, ST st,
-                                           MUL mul) {
-  constexpr int LR = L / RL;
-  float2 v[3][RL];
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int r = 0; r < RL; ++r) v[c][r] = ld(line0 + c * lstride, j + r * LR);
-  if constexpr (RL > 1) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) butterfly<-1, RL, NSL, false>(v[c], j, tw);
-#pragma unroll
-    for (int q = 0; q < RL; ++q) mul(j + q * LR, v[0][q], v[1][q], v[2][q]);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) butterfly<1, RL, NSL, true>(v[c], j, tw);
-  } else {
-    mul(j, v[0][0], v[1][0], v[2][0]);
-  }
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int r = 0; r < RL; ++r) st(line0 + c * lstride, j + r * LR, v[c][r]);
-}
+// ---- launcher --------------------------------------------------------------------------------
 
-// film: one block = C columns kx, three components each, lines = c * C + cc.
-template <int L>
-__global__ void __launch_bounds__(3 * film_cols(L) * L / GBD_E, min_blocks(3 * film_cols(L) * L / GBD_E))
-    film_conv_kernel(ColArgs a, const float2* __restrict__ tw) {
-  constexpr int C = film_cols(L);
-  constexpr int LINES = 3 * C;
-  constexpr int T = LINES * L / GBD_E;
-  constexpr int LS = line_stride<L, false>();
-  constexpr int NP = npasses(L, true);
-  constexpr int RL = NP >= 1 ? radix_at(L, true, NP - 1) : 1;
-  constexpr int NSL = NP >= 1 ? ns_at(L, true, NP - 1) : 1;
-  constexpr int LR = L / RL;
-  constexpr int KY = L / 2 + 1;
-  extern __shared__ float2 sm[];
-  const int kx0 = blockIdx.x * C;
-  const int ny = a.ny, Hx = a.Hx;
-  float2* S = a.dst;
-
-  auto gptr = [&](int line) { return S + (long long)((line / C) * Hx + kx0 + line % C) * ny; };
-  auto gld = [&](int line, int y) {
-    return (y < ny && kx0 + line % C < Hx) ? gptr(line)[y] : make_float2(0.f, 0.f);
-  };
-  auto gst = [&](int line, int y, float2 v) {
-    if (y < ny && kx0 + line % C < Hx) gptr(line)[y] = v;
-  };
-  auto sld = [&](int line, int i) { return sm[line * LS + pad(i)]; };
-  auto sst = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
-
-  auto run_fused = [&](auto ld, auto st) {
-    for (int it = threadIdx.x; it < C * LR; it += T) {
-      const int cc = it / LR, j = it % LR;
-      const int kx = kx0 + cc;
-      auto mul = [&](int ky, float2& m0, float2& m1, float2& m2) {
-        if (kx >= Hx) return;
-        int kyp = ky;
-        float sy = 1.f;
-        if (L > 1 && ky > L / 2) {
-          kyp = L - ky;
-          sy = -1.f;
-        }
-        const float4 k4 = __ldg(a.Kf + (long long)kx * KY + kyp);
-        const float kxy = sy * k4.w;
-        const float2 h0 = make_float2(k4.x * m0.x + kxy * m1.x, k4.x * m0.y + kxy * m1.y);
-        const float2 h1 = make_float2(kxy * m0.x + k4.y * m1.x, kxy * m0.y + k4.y * m1.y);
-        m2 = make_float2(k4.z * m2.x, k4.z * m2.y);
-        m0 = h0;
-        m1 = h1;
-      };
-      fused_item<L, RL, NSL>(cc, C, j, tw, ld, st, mul);
-    }
-  };
-
-  if constexpr (NP <= 1) {
-    run_fused(gld, gst);
-  } else {
-    stockham_pass<-1, false, L, radix_at(L, true, 0), 1, LINES, false, false>(tw, gld, sst);
-    __syncthreads();
-    fwd_passes_smem<-1, L, true, LINES, false, LS, 1, NP - 1>(sm, tw);
-    run_fused(sld, sst);
-    __syncthreads();
-    adj_passes_smem<1, L, true, LINES, false, LS, NP - 1, 1>(sm, tw);
-    stockham_pass<1, true, L, radix_at(L, true, 0), 1, LINES, false, false>(tw, sld, gst);
-  }
-}
-
-// 3D y passes over independent lines l = (c*nz + z)*Hx + kx: forward S (ny) -> T (Py),
-// inverse T (Py) -> S (first ny).
-template <int L, bool INV>
-__global__ void __launch_bounds__(ypass_lines(L) * L / GBD_E, min_blocks(ypass_lines(L) * L / GBD_E))
-    y_pass_kernel(ColArgs a, const float2* __restrict__ tw) {
-  constexpr int LINES = ypass_lines(L);
-  constexpr int LS = line_stride<L, false>();
-  constexpr int NP = npasses(L, false);
-  extern __shared__ float2 sm[];
-  const long long l0 = (long long)blockIdx.x * LINES;
-  const int ny = a.ny;
-  const long long nl = a.lines_total;
-  auto sld = [&](int line, int i) { return sm[line * LS + pad(i)]; };
-  auto sst = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
-  if constexpr (!INV) {
-    auto gld = [&](int line, int y) {
-      return (y < ny && l0 + line < nl) ? a.src[(l0 + line) * ny + y] : make_float2(0.f, 0.f);
-    };
-    auto gst = [&](int line, int i, float2 v) {
-      if (l0 + line < nl) a.dst[(l0 + line) * L + i] = v;
-    };
-    if constexpr (NP == 1) {
-      stockham_pass<-1, false, L, radix_at(L, false, 0), 1, LINES, false, false>(tw, gld, gst);
-    } else {
-      stockham_pass<-1, false, L, radix_at(L, false, 0), 1, LINES, false, false>(tw, gld, sst);
-      __syncthreads();
-      fwd_passes_smem<-1, L, false, LINES, false, LS, 1, NP - 1>(sm, tw);
-      stockham_pass<-1, false, L, radix_at(L, false, NP - 1), ns_at(L, false, NP - 1), LINES, false, false>(tw, sld,
-                                                                                                           gst);
-    }
-  } else {
-    auto gld = [&](int line, int i) {
-      return (l0 + line < nl) ? a.src[(l0 + line) * L + i] : make_float2(0.f, 0.f);
-    };
-    auto gst = [&](int line, int y, float2 v) {
-      if (y < ny && l0 + line < nl) a.dst[(l0 + line) * ny + y] = v;
-    };
-    if constexpr (NP == 1) {
-      stockham_pass<1, true, L, radix_at(L, false, 0), 1, LINES, false, false>(tw, gld, gst);
-    } else {
-      stockham_pass<1, true, L, radix_at(L, false, NP - 1), ns_at(L, false, NP - 1), LINES, false, false>(tw, gld,
-                                                                                                         sst);
-      __syncthreads();
-      adj_passes_smem<1, L, false, LINES, false, LS, NP - 1, 1>(sm, tw);
-      stockham_pass<1, true, L, radix_at(L, false, 0), 1, LINES, false, false>(tw, sld, gst);
-    }
-  }
-}
-
-// 3D z convolution: block = W consecutive columns q of [3][nz][Q], lines c * W + w,
-// interleaved (consecutive threads take consecutive columns).
-template <int L>
-__global__ void __launch_bounds__(3 * zconv_cols(L) * L / GBD_E, min_blocks(3 * zconv_cols(L) * L / GBD_E))
-    z_conv_kernel(ColArgs a, const float2* __restrict__ tw) {
-  constexpr int W = zconv_cols(L);
-  constexpr int LINES = 3 * W;
-  constexpr int T = LINES * L / GBD_E;
-  constexpr int LS = line_stride<L, true>();
-  constexpr int NP = npasses(L, true);
-  constexpr int RL = radix_at(L, true, NP - 1);
-  constexpr int NSL = ns_at(L, true, NP - 1);
-  constexpr int LR = L / RL;
-  constexpr int KZ = L / 2 + 1;
-  extern __shared__ float2 sm[];
-  const long long q0 = (long long)blockIdx.x * W;
-  const int nz = a.nz;
-  const long long Q = a.Q;
-  float2* D = a.dst;
-  auto gld = [&](int line, int z) {
-    const long long q = q0 + line % W;
-    return (z < nz && q < Q) ? D[(long long)((line / W) * nz + z) * Q + q] : make_float2(0.f, 0.f);
-  };
-  auto gst = [&](int line, int z, float2 v) {
-    const long long q = q0 + line % W;
-    if (z < nz && q < Q) D[(long long)((line / W) * nz + z) * Q + q] = v;
-  };
-  auto sld = [&](int line, int i) { return sm[line * LS + pad(i)]; };
-  auto sst = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
-  const int Py = a.Py, KY = a.Py / 2 + 1, Pyq = a.Pyq;
-  auto run_fused = [&](auto ld, auto st) {
-    for (int it = threadIdx.x; it < W * LR; it += T) {
-      const int w = it % W, j = it / W;
-      const long long q = q0 + w;
-      const int kx = (int)(q / Pyq);
-      const int ky = (int)(q - (long long)kx * Pyq);
-      int kyp = ky;
-      float sy = 1.f;
-      if (Py > 1 && ky > Py / 2) {
-        kyp = Py - ky;
-        sy = -1.f;
-      }
-      const float* kbase = a.K3 + ((long long)kx * KY + kyp) * KZ * 6;
-      auto mul = [&](int kz, float2& m0, float2& m1, float2& m2) {
-        if (q >= Q) return;
-        int kzp = kz;
-        float sz = 1.f;
-        if (kz > L / 2) {
-          kzp = L - kz;
-          sz = -1.f;
-        }
-        const float* kp = kbase + kzp * 6;
-        const float2 k01 = __ldg(reinterpret_cast<const float2*>(kp));
-        const float2 k23 = __ldg(reinterpret_cast<const float2*>(kp + 2));
-        const float2 k45 = __ldg(reinterpret_cast<const float2*>(kp + 4));
-        const float kxx = k01.x, kyy = k01.y, kzz = k23.x;
-        const float kxy = sy * k23.y, kxz = sz * k45.x, kyz = sy * sz * k45.y;
-        const float2 h0 = make_float2(kxx * m0.x + kxy * m1.x + kxz * m2.x, kxx * m0.y + kxy * m1.y + kxz * m2.y);
-        const float2 h1 = make_float2(kxy * m0.x + kyy * m1.x + kyz * m2.x, kxy * m0.y + kyy * m1.y + kyz * m2.y);
-        const float2 h2 = make_float2(kxz * m0.x + kyz * m1.x + kzz * m2.x, kxz * m0.y + kyz * m1.y + kzz * m2.y);
-        m0 = h0;
-        m1 = h1;
-        m2 = h2;
-      };
-      fused_item<L, RL, NSL>(w, W, j, tw, ld, st, mul);
-    }
-  };
-  if constexpr (NP == 1) {
-    run_fused(gld, gst);
-  } else {
-    stockham_pass<-1, false, L, radix_at(L, true, 0), 1, LINES, true, false>(tw, gld, sst);
-    __syncthreads();
-    fwd_passes_smem<-1, L, true, LINES, true, LS, 1, NP - 1>(sm, tw);
-    run_fused(sld, sst);
-    __syncthreads();
-    adj_passes_smem<1, L, true, LINES, true, LS, NP - 1, 1>(sm, tw);
-    stockham_pass<1, true, L, radix_at(L, true, 0), 1, LINES, true, false>(tw, sld, gst);
-  }
-}
-
-// ---- launchers ------------------------------------------------------------------------------
-
-template <class K>
-static void prep(K k, size_t smem) {
-  static thread_local const void* done[64] = {nullptr};
-  for (auto& d : done) {
-    if (d == (const void*)k) return;
-    if (d == nullptr) {
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      d = (const void*)k;
-      return;
-    }
-  }
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-
-template <int LX>
-static void row_launch_t(const RowArgs& a, const float2* tw, cudaStream_t st) {
-  constexpr int RB = row_rb(LX);
+template <int LX, int RB>
+static void row_launch_t(const RowArgs* a, const float2* tw, cudaStream_t st) {
   constexpr int T = 3 * RB * LX / GBD_E;
   const size_t smem = (size_t)3 * RB * line_stride<LX, true>() * sizeof(float2);
-  prep(row_kernel<LX>, smem);
-  row_kernel<LX><<<(a.rows + RB - 1) / RB, T, smem, st>>>(a, tw);
+  prep(row_kernel<LX, RB>, smem);
+  if (a) row_kernel<LX, RB><<<(a->rows + RB - 1) / RB, T, smem, st>>>(*a, tw);
 }
 
-template <int L>
-static void film_launch_t(const ColArgs& a, const float2* tw, cudaStream_t st) {
-  constexpr int C = film_cols(L);
-  constexpr int T = 3 * C * L / GBD_E;
-  const size_t smem = (size_t)3 * C * line_stride<L, false>() * sizeof(float2);
-  prep(film_conv_kernel<L>, smem);
-  film_conv_kernel<L><<<(a.Hx + C - 1) / C, T, smem, st>>>(a, tw);
-}
+#define GBD_ROW_CASE(LX)                                        \
+  case LX:                                                      \
+    if (var <= 0)                                               \
+      row_launch_t<LX, row_rb(LX, 0)>(a, tw, st);               \
+    if (var != 0)                                               \
+      row_launch_t<LX, row_rb(LX, 1)>(a, tw, st);               \
+    return true;
 
-template <int L, bool INV>
-static void ypass_launch_t(const ColArgs& a, const float2* tw, cudaStream_t st) {
-  constexpr int C = ypass_lines(L);
-  constexpr int T = C * L / GBD_E;
-  const size_t smem = (size_t)C * line_stride<L, false>() * sizeof(float2);
-  prep(y_pass_kernel<L, INV>, smem);
-  y_pass_kernel<L, INV><<<(unsigned)((a.lines_total + C - 1) / C), T, smem, st>>>(a, tw);
-}
-
-template <int L>
-static void zconv_launch_t(const ColArgs& a, const float2* tw, cudaStream_t st) {
-  constexpr int W = zconv_cols(L);
-  constexpr int T = 3 * W * L / GBD_E;
-  const size_t smem = (size_t)3 * W * line_stride<L, true>() * sizeof(float2);
-  prep(z_conv_kernel<L>, smem);
-  z_conv_kernel<L><<<(unsigned)((a.Q + W - 1) / W), T, smem, st>>>(a, tw);
-}
-
-bool launch_row(int Lx, const RowArgs& a, const float2* tw, cudaStream_t st) {
+// a == nullptr only prepares the kernels (both variants when var < 0).
+static bool row_dispatch(int Lx, int var, const RowArgs* a, const float2* tw, cudaStream_t st) {
   switch (Lx) {
-    case 1: row_launch_t<1>(a, tw, st); return true;
-    case 2: row_launch_t<2>(a, tw, st); return true;
-    case 4: row_launch_t<4>(a, tw, st); return true;
-    case 8: row_launch_t<8>(a, tw, st); return true;
-    case 16: row_launch_t<16>(a, tw, st); return true;
-    case 32: row_launch_t<32>(a, tw, st); return true;
-    case 64: row_launch_t<64>(a, tw, st); return true;
-    case 128: row_launch_t<128>(a, tw, st); return true;
-    case 256: row_launch_t<256>(a, tw, st); return true;
-    case 512: row_launch_t<512>(a, tw, st); return true;
-    case 1024: row_launch_t<1024>(a, tw, st); return true;
-    case 2048: row_launch_t<2048>(a, tw, st); return true;
-    case 4096: row_launch_t<4096>(a, tw, st); return true;
+    GBD_ROW_CASE(1)
+    GBD_ROW_CASE(2)
+    GBD_ROW_CASE(4)
+    GBD_ROW_CASE(8)
+    GBD_ROW_CASE(16)
+    GBD_ROW_CASE(32)
+    GBD_ROW_CASE(64)
+    GBD_ROW_CASE(128)
+    GBD_ROW_CASE(256)
+    GBD_ROW_CASE(512)
+    GBD_ROW_CASE(1024)
+    GBD_ROW_CASE(2048)
+    GBD_ROW_CASE(4096)
     default: return false;
   }
 }
 
-bool launch_film_conv(const ColArgs& a, const float2* tw, cudaStream_t st) {
-  switch (a.Py) {
-    case 1: film_launch_t<1>(a, tw, st); return true;
-    case 4: film_launch_t<4>(a, tw, st); return true;
-    case 8: film_launch_t<8>(a, tw, st); return true;
-    case 16: film_launch_t<16>(a, tw, st); return true;
-    case 32: film_launch_t<32>(a, tw, st); return true;
-    case 64: film_launch_t<64>(a, tw, st); return true;
-    case 128: film_launch_t<128>(a, tw, st); return true;
-    case 256: film_launch_t<256>(a, tw, st); return true;
-    case 512: film_launch_t<512>(a, tw, st); return true;
-    case 1024: film_launch_t<1024>(a, tw, st); return true;
-    case 2048: film_launch_t<2048>(a, tw, st); return true;
-    case 4096: film_launch_t<4096>(a, tw, st); return true;
-    default: return false;
-  }
+bool launch_row(int Lx, int var, const RowArgs& a, const float2* tw, cudaStream_t st) {
+  return row_dispatch(Lx, var, &a, tw, st);
 }
-
-template <bool INV>
-static bool ypass_dispatch(const ColArgs& a, const float2* tw, cudaStream_t st) {
-  switch (a.Py) {
-    case 4: ypass_launch_t<4, INV>(a, tw, st); return true;
-    case 8: ypass_launch_t<8, INV>(a, tw, st); return true;
-    case 16: ypass_launch_t<16, INV>(a, tw, st); return true;
-    case 32: ypass_launch_t<32, INV>(a, tw, st); return true;
-    case 64: ypass_launch_t<64, INV>(a, tw, st); return true;
-    case 128: ypass_launch_t<128, INV>(a, tw, st); return true;
-    case 256: ypass_launch_t<256, INV>(a, tw, st); return true;
-    case 512: ypass_launch_t<512, INV>(a, tw, st); return true;
-    case 1024: ypass_launch_t<1024, INV>(a, tw, st); return true;
-    case 2048: ypass_launch_t<2048, INV>(a, tw, st); return true;
-    case 4096: ypass_launch_t<4096, INV>(a, tw, st); return true;
-    default: return false;
-  }
-}
-
-bool launch_y_fwd(const ColArgs& a, const float2* tw, cudaStream_t st) { return ypass_dispatch<false>(a, tw, st); }
-bool launch_y_inv(const ColArgs& a, const float2* tw, cudaStream_t st) { return ypass_dispatch<true>(a, tw, st); }
-
-bool launch_z_conv(const ColArgs& a, const float2* tw, cudaStream_t st) {
-  switch (a.Pz) {
-    case 4: zconv_launch_t<4>(a, tw, st); return true;
-    case 8: zconv_launch_t<8>(a, tw, st); return true;
-    case 16: zconv_launch_t<16>(a, tw, st); return true;
-    case 32: zconv_launch_t<32>(a, tw, st); return true;
-    case 64: zconv_launch_t<64>(a, tw, st); return true;
-    case 128: zconv_launch_t<128>(a, tw, st); return true;
-    case 256: zconv_launch_t<256>(a, tw, st); return true;
-    case 512: zconv_launch_t<512>(a, tw, st); return true;
-    case 1024: zconv_launch_t<1024>(a, tw, st); return true;
-    case 2048: zconv_launch_t<2048>(a, tw, st); return true;
-    case 4096: zconv_launch_t<4096>(a, tw, st); return true;
-    default: return false;
-  }
-}
+bool prepare_row(int Lx) { return row_dispatch(Lx, -1, nullptr, nullptr, nullptr); }
 
 }  // namespace gbd

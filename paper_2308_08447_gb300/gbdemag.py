@@ -52,6 +52,12 @@ _SIG = {
     "gbd_plan_dims": [ctypes.POINTER(gbd_mesh_desc), ctypes.POINTER(_I)],
     "gbd_kernel_spectrum_host": [ctypes.POINTER(gbd_mesh_desc), ctypes.POINTER(_D), ctypes.c_size_t],
     "gbd_demag_noalloc": [_P, _P, _P, _P],
+    "gbd_mesh_autotune": [_P, _P],
+    "gbd_mesh_get_tuning": [_P, ctypes.POINTER(_I)],
+    "gbd_mesh_set_tuning": [_P, ctypes.POINTER(_I)],
+    "gbd_batch_create": [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)],
+    "gbd_batch_run": [_P, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_D), _P],
+    "gbd_batch_destroy": [_P],
     "gbd_mesh_set_timing": [_P, _I],
     "gbd_mesh_read_timing": [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)],
 }
@@ -166,6 +172,40 @@ def gbd_mesh_destroy(mesh):
     _check(load().gbd_mesh_destroy(mesh))
 
 
+def gbd_mesh_autotune(mesh, stream=None):
+    _check(load().gbd_mesh_autotune(mesh, _stream_ptr(stream)))
+
+
+def gbd_mesh_get_tuning(mesh):
+    out = (ctypes.c_int * 4)()
+    _check(load().gbd_mesh_get_tuning(mesh, out))
+    return tuple(out)
+
+
+def gbd_mesh_set_tuning(mesh, variants):
+    arr = (ctypes.c_int * 4)(*[int(v) for v in variants])
+    _check(load().gbd_mesh_set_tuning(mesh, arr))
+
+
+def gbd_batch_create(meshes):
+    arr = (ctypes.c_void_p * len(meshes))(*[m.value if isinstance(m, ctypes.c_void_p) else m for m in meshes])
+    out = ctypes.c_void_p()
+    _check(load().gbd_batch_create(arr, len(meshes), ctypes.byref(out)))
+    return out
+
+
+def gbd_batch_run(batch, m_list, shapes, nsteps, dts, stream=None):
+    n = len(m_list)
+    ptrs = (ctypes.c_void_p * n)(*[_field_ptr(t, s, "m[%d]" % i).value for i, (t, s) in enumerate(zip(m_list, shapes))])
+    steps = (ctypes.c_int * n)(*[int(v) for v in nsteps])
+    dt = (ctypes.c_double * n)(*[float(v) for v in dts])
+    _check(load().gbd_batch_run(batch, ptrs, steps, dt, _stream_ptr(stream)))
+
+
+def gbd_batch_destroy(batch):
+    _check(load().gbd_batch_destroy(batch))
+
+
 def gbd_mesh_set_timing(mesh, enable):
     _check(load().gbd_mesh_set_timing(mesh, 1 if enable else 0))
 
@@ -229,9 +269,35 @@ class Mesh:
     def llg_step(self, m, nsteps, dt, stream=None):
         gbd_llg_step(self.handle, m, nsteps, dt, self.shape, stream)
 
+    def autotune(self, stream=None):
+        gbd_mesh_autotune(self.handle, stream)
+        return gbd_mesh_get_tuning(self.handle)
+
     def close(self):
         if self.handle is not None:
             gbd_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many meshes advanced together with one CUDA-graph launch per run (gbd_batch_*)."""
+
+    def __init__(self, meshes):
+        self.meshes = list(meshes)
+        self.handle = gbd_batch_create([m.handle for m in self.meshes])
+
+    def run(self, m_list, nsteps, dts, stream=None):
+        gbd_batch_run(self.handle, m_list, [m.shape for m in self.meshes], nsteps, dts, stream)
+
+    def close(self):
+        if self.handle is not None:
+            gbd_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
