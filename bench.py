@@ -301,6 +301,123 @@ def cpu_baseline(spec, m0, repeats=1):
                       "single-threaded FFT); %.1f s" % (repeats, 4 * repeats, t)}
 
 
+def run_batch(args):
+    """64 uneven meshes (nx, ny in {64..512} step 32, nz in {1, 2, 4, 8, 16}, cubic 2-5 nm cells,
+    Ms in [4e5, 1.4e6] A/m, random unit m, 100 RK4 steps each): the plain path (each mesh alone,
+    one gbd_llg_step call after another) against one batched CUDA-graph launch (gbd_batch_run)."""
+    import numpy as np
+    import torch
+
+    from paper_2308_08447_gb300 import gbdemag
+    from paper_2308_08447_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    gbdemag.load()
+    specs = W.batch_meshes(count=args.batch_count, seed=4, steps=args.llg_steps if args.llg_steps != 1000 else 100)
+    t0 = time.perf_counter()
+    meshes = [gbdemag.Mesh(s.n, s.cell, s.Ms, A_ex=s.A_ex, alpha=s.alpha) for s in specs]
+    tunings = [m.autotune() for m in meshes]
+    setup_s = time.perf_counter() - t0
+    init = [torch.from_numpy(W.random_unit(s.n, s.seed)).cuda() for s in specs]
+    steps = [s.steps for s in specs]
+    dts = [s.dt for s in specs]
+    evals = sum(s.cells * 4 * s.steps for s in specs)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def timed(fn, reps):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return ts
+
+    plain_m = [m.clone() for m in init]
+
+    def plain():
+        for mesh, m, n, dt in zip(meshes, plain_m, steps, dts):
+            mesh.llg_step(m, n, dt)
+
+    batch = gbdemag.Batch(meshes)
+    batch_m = [m.clone() for m in init]
+
+    def batched():
+        batch.run(batch_m, steps, dts)
+
+    # one run of each from the same initial state: results must be bit-identical
+    plain()
+    batched()
+    torch.cuda.synchronize()
+    identical = all(torch.equal(a, b) for a, b in zip(plain_m, batch_m))
+    for _ in range(max(0, args.warmup - 1)):
+        plain()
+        batched()
+    sampler = ClockSampler(0)
+    sampler.start()
+    t_plain = timed(plain, args.steps)
+    t_batch = timed(batched, args.steps)
+    clocks = sampler.stop()
+    v_plain = evals * len(t_plain) / sum(t_plain) / 1e9
+    v_batch = evals * len(t_batch) / sum(t_batch) / 1e9
+    batch.close()
+    for m in meshes:
+        m.close()
+    return {"metric": METRIC, "value": round(v_batch, 3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * sum(t_batch) / len(t_batch), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "batched: %d uneven meshes, %d RK4 steps each, one CUDA-graph launch per run"
+                                   % (len(specs), steps[0]),
+                       "cells": sum(s.cells for s in specs), "demag_evals_per_step": evals,
+                       "l2": "flushed (512 MB write) before each step", "setup_s": round(setup_s, 1)},
+            "plain_path": {"value": round(v_plain, 3), "unit": UNIT,
+                           "ms_per_step": round(1e3 * sum(t_plain) / len(t_plain), 3)},
+            "speedup_vs_plain": round(v_batch / v_plain, 3), "results_bit_identical": bool(identical),
+            "tunings": {"%dx%dx%d" % s.n: list(t) for s, t in zip(specs, tunings)},
+            "gpu_launches": sum(1 + 8 * n for n in steps) * args.steps, "clocks": clocks}
+
+
+def run_serve(args):
+    """Poisson arrivals (200 requests/s) of relaxation jobs (alpha = 0.5, 200-2000 steps, mesh
+    sides log-uniform 64..1024, nz 1..16), admitted by a 150 GB budget, continuously batched;
+    latency percentiles and throughput against the plain path (each job alone, in order)."""
+    import numpy as np
+    import torch
+
+    from paper_2308_08447_gb300 import serve
+
+    torch.cuda.set_device(0)
+    os.environ.setdefault("GBD_KERNEL_CACHE_BYTES", str(64 << 30))
+    ex = serve.GpuExecutor()
+    jobs = serve.make_jobs(args.requests, args.rate, seed=5)
+    t0 = time.perf_counter()
+    ex.prewarm(jobs)
+    setup_s = time.perf_counter() - t0
+    sampler = ClockSampler(0)
+    sampler.start()
+    srv = serve.Server(ex, 150e9, chunk=args.chunk)
+    served = srv.run([serve.Job(j.id, j.spec, j.arrival) for j in jobs])
+    ex.close()
+    plain = serve.run_plain(ex, [serve.Job(j.id, j.spec, j.arrival) for j in jobs])
+    clocks = sampler.stop()
+    by_id = {j.id: j for j in plain}
+    identical = all(np.array_equal(j.result, by_id[j.id].result) for j in served)
+    s_served, s_plain = serve.summarize(served), serve.summarize(plain)
+    return {"metric": METRIC, "value": round(s_served["gcell_demag_per_s"], 3), "unit": UNIT, "n_gpus": 1,
+            "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "served: %d Poisson-arrival jobs at %.0f/s, continuous batching, %d-step chunks, "
+                                   "150 GB budget" % (len(jobs), args.rate, args.chunk),
+                       "setup_s": round(setup_s, 1)},
+            "served": s_served, "plain_path": s_plain, "results_bit_identical": bool(identical),
+            "max_active": max(a for _, a, _ in srv.trace), "iterations": len(srv.trace), "clocks": clocks}
+
+
 def run_reference(args):
     rank, world, local = _dist_env()
     if rank != 0:
@@ -334,9 +451,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--llg-steps", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="film", choices=["film", "batch", "serve"])
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--chunk", type=int, default=50)
     args = ap.parse_args()
     if args.impl == "reference":
         res = run_reference(args)
+    elif args.workload == "batch":
+        res = run_batch(args)
+    elif args.workload == "serve":
+        res = run_serve(args)
     else:
         res = run_ours(args)
     if res is not None:

@@ -79,7 +79,10 @@ gbd_status gbd_mesh_bytes(const gbd_mesh_desc* desc, size_t* out);
  * the near field, Gauss-Legendre cell-pair quadrature beyond 8 cell sizes --, transforms
  * it in FP64, folds in -1/(Px Py Pz), packs the stored quadrant (Appendix A's convolution
  * kernel, (nx+1)(ny+1)(nz+1)-sized up to padding) and copies it to the device in FP32.
- * Blocks until the copy is done. Must precede the compute calls. */
+ * Blocks until the copy is done. Must precede the compute calls. The packed FP32 spectrum is
+ * kept in a process-wide host cache keyed by (nx, ny, nz, dx, dy, dz), so another mesh of
+ * the same geometry only pays the copy; least recently used entries are dropped beyond
+ * GBD_KERNEL_CACHE_BYTES (environment variable, default 4 GiB). */
 gbd_status gbd_set_kernel(gbd_mesh* mesh, void* stream);
 
 /* H = H_d(M) of Eq. 1. M, H: device [3][nz][ny][nx] float32, A/m; M and H must not overlap. */

@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <string>
@@ -385,16 +386,81 @@ gbd_status gbd_mesh_destroy(gbd_mesh* m) {
   return GBD_OK;
 }
 
+// Host cache of packed FP32 kernel spectra keyed by geometry (mesh size and cell), so meshes
+// of a geometry seen before skip the FP64 tensor and its transform. Least recently used
+// entries are dropped beyond GBD_KERNEL_CACHE_BYTES (environment, default 4 GiB).
+namespace {
+struct GeoKey {
+  int nx, ny, nz;
+  double dx, dy, dz;
+  bool operator<(const GeoKey& o) const {
+    if (nx != o.nx) return nx < o.nx;
+    if (ny != o.ny) return ny < o.ny;
+    if (nz != o.nz) return nz < o.nz;
+    if (dx != o.dx) return dx < o.dx;
+    if (dy != o.dy) return dy < o.dy;
+    return dz < o.dz;
+  }
+};
+struct SpecEntry {
+  std::shared_ptr<const std::vector<float>> data;
+  unsigned long long last_use = 0;
+};
+std::mutex g_spec_mu;
+std::map<GeoKey, SpecEntry> g_spec;
+unsigned long long g_spec_clock = 0;
+
+size_t spec_cache_limit() {
+  const char* v = std::getenv("GBD_KERNEL_CACHE_BYTES");
+  if (v && *v) return (size_t)std::strtoull(v, nullptr, 10);
+  return (size_t)4 << 30;
+}
+
+std::shared_ptr<const std::vector<float>> spec_cache_get(const GeoKey& k) {
+  std::lock_guard<std::mutex> lock(g_spec_mu);
+  auto it = g_spec.find(k);
+  if (it == g_spec.end()) return nullptr;
+  it->second.last_use = ++g_spec_clock;
+  return it->second.data;
+}
+
+void spec_cache_put(const GeoKey& k, std::shared_ptr<const std::vector<float>> d) {
+  std::lock_guard<std::mutex> lock(g_spec_mu);
+  g_spec[k] = SpecEntry{d, ++g_spec_clock};
+  const size_t limit = spec_cache_limit();
+  for (;;) {
+    size_t total = 0;
+    auto oldest = g_spec.end();
+    for (auto it = g_spec.begin(); it != g_spec.end(); ++it) {
+      total += it->second.data->size() * sizeof(float);
+      if (oldest == g_spec.end() || it->second.last_use < oldest->second.last_use) oldest = it;
+    }
+    if (total <= limit || g_spec.size() <= 1) break;
+    g_spec.erase(oldest);
+  }
+}
+}  // namespace
+
 gbd_status gbd_set_kernel(gbd_mesh* m, void* stream) {
   if (!m) return fail(GBD_EINVAL, "mesh is NULL");
   gbd_status s = check_device(m);
   if (s != GBD_OK) return s;
   const gbd::Plan& p = m->p;
+  const GeoKey key{p.nx, p.ny, p.nz, m->d.dx, m->d.dy, m->d.dz};
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (auto hit = spec_cache_get(key)) {
+    cudaError_t e = cudaMemcpyAsync(m->K, hit->data(), p.bytes_K, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel upload");
+    m->kernel_set = true;
+    return GBD_OK;
+  }
   std::vector<double> spec;
   if (!gbdt::kernel_spectrum(p, m->d.dx, m->d.dy, m->d.dz, spec)) return fail(GBD_ENOMEM, "host allocation failed");
   const size_t plane = (size_t)p.Ky * p.Hx;
   const size_t comp = (size_t)p.Kz * plane;
-  std::vector<float> packed;
+  auto packed_ptr = std::make_shared<std::vector<float>>();
+  std::vector<float>& packed = *packed_ptr;
   try {
     packed.resize(p.bytes_K / sizeof(float));
   } catch (...) {
@@ -415,10 +481,10 @@ gbd_status gbd_set_kernel(gbd_mesh* m, void* stream) {
             packed[(((size_t)kx * p.Ky + ky) * p.Kz + kz) * 6 + c] =
                 (float)spec[c * comp + (size_t)kz * plane + (size_t)ky * p.Hx + kx];
   }
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMemcpyAsync(m->K, packed.data(), p.bytes_K, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "kernel upload");
+  spec_cache_put(key, packed_ptr);
   m->kernel_set = true;
   return GBD_OK;
 }
