@@ -400,7 +400,7 @@ def run_serve(args):
     setup_s = time.perf_counter() - t0
     sampler = ClockSampler(0)
     sampler.start()
-    srv = serve.Server(ex, 150e9, chunk=args.chunk)
+    srv = serve.Server(ex, 150e9, chunk=args.chunk, max_active=args.max_active or None)
     served = srv.run([serve.Job(j.id, j.spec, j.arrival) for j in jobs])
     ex.close()
     plain = serve.run_plain(ex, [serve.Job(j.id, j.spec, j.arrival) for j in jobs])
@@ -413,7 +413,7 @@ def run_serve(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "served: %d Poisson-arrival jobs at %.0f/s, continuous batching, %d-step chunks, "
                                    "150 GB budget" % (len(jobs), args.rate, args.chunk),
-                       "setup_s": round(setup_s, 1)},
+                       "max_active_cap": args.max_active or None, "setup_s": round(setup_s, 1)},
             "served": s_served, "plain_path": s_plain, "results_bit_identical": bool(identical),
             "max_active": max(a for _, a, _ in srv.trace), "iterations": len(srv.trace), "clocks": clocks}
 
@@ -456,6 +456,7 @@ def main():
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--chunk", type=int, default=50)
+    ap.add_argument("--max-active", type=int, default=8, help="served jobs per iteration (0: no cap)")
     args = ap.parse_args()
     if args.impl == "reference":
         res = run_reference(args)

@@ -42,10 +42,14 @@ class Job:
 class Server:
     """Admission by memory budget, per-iteration batching of all active jobs, retirement."""
 
-    def __init__(self, executor, budget_bytes, chunk=50, clock=time.perf_counter, sleep=time.sleep):
+    def __init__(self, executor, budget_bytes, chunk=50, max_active=None, clock=time.perf_counter,
+                 sleep=time.sleep):
         self.ex = executor
         self.budget = int(budget_bytes)
         self.chunk = int(chunk)
+        # at most this many jobs share an iteration (None: as many as the budget admits);
+        # a cap keeps early jobs from being slowed by every later arrival
+        self.max_active = max_active
         self.clock = clock
         self.sleep = sleep
         self.used = 0
@@ -70,7 +74,8 @@ class Server:
             still = []
             for j in waiting:
                 b = self.ex.bytes_for(j)
-                if self.used + b <= self.budget:
+                full = self.max_active is not None and len(active) >= self.max_active
+                if not full and self.used + b <= self.budget:
                     self.ex.admit(j)
                     self.used += b
                     j.admitted = self.clock() - t0
@@ -213,13 +218,15 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--chunk", type=int, default=50)
+    ap.add_argument("--max-active", type=int, default=8)
     ap.add_argument("--max-side", type=int, default=1024)
     args = ap.parse_args(argv)
     os.environ.setdefault("GBD_KERNEL_CACHE_BYTES", str(64 << 30))
     ex = GpuExecutor()
     jobs = make_jobs(args.requests, args.rate, args.seed, args.max_side)
     ex.prewarm(jobs)
-    served = Server(ex, args.budget_gb * 1e9, chunk=args.chunk).run([Job(j.id, j.spec, j.arrival) for j in jobs])
+    served = Server(ex, args.budget_gb * 1e9, chunk=args.chunk, max_active=args.max_active or None).run(
+        [Job(j.id, j.spec, j.arrival) for j in jobs])
     ex.close()
     plain = run_plain(ex, [Job(j.id, j.spec, j.arrival) for j in jobs])
     same = all(np.array_equal(a.result, b.result) for a, b in

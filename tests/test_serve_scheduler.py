@@ -93,6 +93,18 @@ def test_budget_respected_and_late_jobs_join_in_flight():
     assert s["p99_s"] >= s["p50_s"] > 0
 
 
+def test_max_active_caps_concurrency_and_keeps_arrival_order():
+    clk = SimClock()
+    ex = FakeExecutor(clk)
+    jobs = [_job(i, 100, 100 + 10 * i, 0.0) for i in range(6)]
+    srv = Server(ex, budget_bytes=10 ** 12, chunk=25, max_active=2, clock=clk, sleep=clk.sleep)
+    done = {j.id: j for j in srv.run(jobs)}
+    assert max(a for _, a, _ in srv.trace) == 2
+    assert ex.admitted == list(range(6))
+    # the first two finish before the last two are even admitted
+    assert done[1].finished <= done[4].admitted + 1e-12
+
+
 def test_job_larger_than_budget_is_refused():
     clk = SimClock()
     srv = Server(FakeExecutor(clk), budget_bytes=1000, clock=clk, sleep=clk.sleep)
