@@ -243,6 +243,65 @@ __device__ __forceinline__ void stockham_pass(const float2* __restrict__ tw, LD 
   }
 }
 
+// The same pass in place in shared memory, with the padded addresses of a butterfly's R
+// elements formed as one base plus compile-time strides where the padding allows it:
+//   natural set  j + r L/R        : pad = pad(j) + r (L/R + L/R/16)     when L/R % 16 == 0
+//   scattered set (j-k) R + k + q Ns: pad = pad(base) + q (Ns + Ns/16)   when Ns % 16 == 0,
+//                                     pad = 17 j + q                      when Ns = 1, R = 16
+// (other cases compute pad per element).
+template <int S, bool ADJ, int L, int R, int Ns, int LINES, bool LF, int LS>
+__device__ __forceinline__ void stockham_pass_sm(float2* sm, const float2* __restrict__ tw) {
+  constexpr int LR = L / R;
+  constexpr int NB = GBD_E / R;
+  constexpr int T = LINES * L / GBD_E;
+  constexpr bool NAT_CONST = (LR % 16 == 0);
+  constexpr bool SCA_CONST = (Ns % 16 == 0) || (Ns == 1 && R == 16);
+  constexpr int NAT_STRIDE = LR + LR / 16;
+  constexpr int SCA_STRIDE = (Ns == 1) ? 1 : Ns + Ns / 16;
+  float2 v[NB][R];
+  int nat0[NB], sca0[NB], bj[NB];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int b = threadIdx.x + i * T;
+    int line, j;
+    if (LF) {
+      line = b % LINES;
+      j = b / LINES;
+    } else {
+      line = b / LR;
+      j = b % LR;
+    }
+    const int k = j % Ns;
+    const int lb = line * LS;
+    const int base = (j - k) * R + k;
+    bj[i] = j;
+    nat0[i] = lb + (NAT_CONST ? pad(j) : j);
+    sca0[i] = lb + (SCA_CONST ? (Ns == 1 ? 17 * j : pad(base)) : base);
+    auto nat = [&](int r) { return NAT_CONST ? nat0[i] + r * NAT_STRIDE : lb + pad(j + r * LR); };
+    auto sca = [&](int q) { return SCA_CONST ? sca0[i] + q * SCA_STRIDE : lb + pad(base + q * Ns); };
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[i][r] = sm[ADJ ? sca(r) : nat(r)];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int j = bj[i];
+    const int k = j % Ns;
+    butterfly<S, R, Ns, ADJ>(v[i], k, tw);
+    const int lb_nat = nat0[i] - (NAT_CONST ? pad(j) : j);   // line base
+    const int lb_sca = sca0[i] - (SCA_CONST ? (Ns == 1 ? 17 * j : pad((j - k) * R + k)) : (j - k) * R + k);
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      int addr;
+      if (ADJ)
+        addr = NAT_CONST ? nat0[i] + q * NAT_STRIDE : lb_nat + pad(j + q * LR);
+      else
+        addr = SCA_CONST ? sca0[i] + q * SCA_STRIDE : lb_sca + pad((j - k) * R + k + q * Ns);
+      sm[addr] = v[i][q];
+    }
+  }
+}
+
 // Passes [P, PEND) of the forward chain (sign S) in place in shared memory; LS is the
 // caller's line stride in float2 units.
 template <int S, int L, bool CONV, int LINES, bool LF, int LS, int P, int PEND>
@@ -250,9 +309,7 @@ __device__ __forceinline__ void fwd_passes_smem(float2* sm, const float2* __rest
   if constexpr (P < PEND) {
     constexpr int R = radix_at(L, CONV, P);
     constexpr int Ns = ns_at(L, CONV, P);
-    auto ld = [&](int line, int i) { return sm[line * LS + pad(i)]; };
-    auto st = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
-    stockham_pass<S, false, L, R, Ns, LINES, LF, true>(tw, ld, st);
+    stockham_pass_sm<S, false, L, R, Ns, LINES, LF, LS>(sm, tw);
     __syncthreads();
     fwd_passes_smem<S, L, CONV, LINES, LF, LS, P + 1, PEND>(sm, tw);
   }
@@ -264,9 +321,7 @@ __device__ __forceinline__ void adj_passes_smem(float2* sm, const float2* __rest
   if constexpr (P > PEND) {
     constexpr int R = radix_at(L, CONV, P - 1);
     constexpr int Ns = ns_at(L, CONV, P - 1);
-    auto ld = [&](int line, int i) { return sm[line * LS + pad(i)]; };
-    auto st = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
-    stockham_pass<S, true, L, R, Ns, LINES, LF, true>(tw, ld, st);
+    stockham_pass_sm<S, true, L, R, Ns, LINES, LF, LS>(sm, tw);
     __syncthreads();
     adj_passes_smem<S, L, CONV, LINES, LF, LS, P - 1, PEND>(sm, tw);
   }
