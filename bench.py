@@ -130,7 +130,8 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("gbd_fft.cuh", "gbd_kernels.cuh", "gbd_launch.cuh", "gbd_row.cu", "gbd_conv.cu", "gbd_ypass.cu"):
+    for f in ("gbd_fft.cuh", "gbd_tc.cuh", "gbd_kernels.cuh", "gbd_launch.cuh", "gbd_row.cu", "gbd_conv.cu",
+              "gbd_ypass.cu"):
         with open(os.path.join(ROOT, "paper_2308_08447_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -418,6 +419,86 @@ def run_serve(args):
             "max_active": max(a for _, a, _ in srv.trace), "iterations": len(srv.trace), "clocks": clocks}
 
 
+def run_3d(args):
+    """512 x 512 x 64 cells of 4 nm, Ms = 8e5 A/m, random unit m: one demag evaluation and 100 RK4
+    steps with FP32 stages and with split-BF16 tensor-core stages. The demag error of each is
+    taken against the FP64 oracle's FFT convolution of the full mesh (--oracle-3d); the 100-step
+    error against the oracle's RK4 run is taken on a 64 x 64 x 8 mesh of the same material."""
+    import numpy as np
+    import torch
+
+    from paper_2308_08447_gb300 import gbdemag
+    from paper_2308_08447_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    gbdemag.load()
+    spec = W.large_3d()
+    nsteps = 100
+    m0 = W.random_unit(spec.n, spec.seed)
+    res = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "data": "synthetic", "steps": args.steps, "warmup": args.warmup,
+           "config": {"workload": "3D 512x512x64, 4 nm cubes: 1 demag + %d RK4 steps, FP32 vs split-BF16" % nsteps}}
+    stream = torch.cuda.current_stream()
+    H = {}
+    for name, prec in (("fp32", gbdemag.GBD_FP32), ("split_bf16", gbdemag.GBD_SPLIT_BF16)):
+        mesh = gbdemag.Mesh(spec.n, spec.cell, spec.Ms, A_ex=spec.A_ex, alpha=spec.alpha, precision=prec)
+        mesh.autotune()
+        M = torch.from_numpy(spec.Ms * m0).cuda()
+        Hd = torch.empty_like(M)
+        for _ in range(args.warmup):
+            mesh.demag(M, Hd)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            mesh.demag(M, Hd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_demag = e0.elapsed_time(e1) / 1e3 / args.steps
+        H[name] = Hd.cpu().numpy()
+        m = torch.from_numpy(m0).cuda()
+        mesh.llg_step(m, 2, spec.dt)
+        m = torch.from_numpy(m0).cuda()
+        e0.record(stream)
+        mesh.llg_step(m, nsteps, spec.dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_llg = e0.elapsed_time(e1) / 1e3
+        res[name] = {"demag_ms": round(t_demag * 1e3, 3), "demag_gcell_per_s": round(spec.cells / t_demag / 1e9, 3),
+                     "llg_100_steps_s": round(t_llg, 4),
+                     "llg_gcell_demag_per_s": round(spec.cells * 4 * nsteps / t_llg / 1e9, 3),
+                     "tuning": list(gbdemag.gbd_mesh_get_tuning(mesh.handle))}
+        res[name + "_m_after_100"] = m.cpu().numpy()
+        mesh.close()
+    d = res.pop("split_bf16_m_after_100") - res.pop("fp32_m_after_100")
+    res["split_vs_fp32_m_after_100_max_abs"] = float(np.abs(d).max())
+    res["value"] = res["fp32"]["llg_gcell_demag_per_s"]
+    res["dtype"] = "f32"
+    if args.oracle_3d:
+        from oracle import conv as C
+        from oracle import tensor as T
+        t0 = time.perf_counter()
+        Href = C.fft_conv((spec.Ms * m0).astype(np.float64), T.tensor_all_offsets(spec.n, spec.cell))
+        nrm = np.sqrt((Href ** 2).sum(0)).max()
+        for name in ("fp32", "split_bf16"):
+            res[name]["demag_e_inf_vs_fp64_oracle"] = float(np.sqrt(((H[name] - Href) ** 2).sum(0)).max() / nrm)
+        res["oracle_s"] = round(time.perf_counter() - t0, 1)
+    # 100 steps against the FP64 oracle on a 64 x 64 x 8 mesh of the same material
+    from oracle import llg as L
+    from oracle import tensor as T
+    small = (64, 64, 8)
+    ms0 = W.random_unit(small, spec.seed)
+    Nf = T.tensor_all_offsets(small, spec.cell)
+    want = L.llg_run(ms0.astype(np.float64), nsteps, spec.dt, Nf, spec.cell, spec.Ms, spec.A_ex, spec.alpha)
+    for name, prec in (("fp32", gbdemag.GBD_FP32), ("split_bf16", gbdemag.GBD_SPLIT_BF16)):
+        mesh = gbdemag.Mesh(small, spec.cell, spec.Ms, A_ex=spec.A_ex, alpha=spec.alpha, precision=prec)
+        m = torch.from_numpy(ms0).cuda()
+        mesh.llg_step(m, nsteps, spec.dt)
+        got = m.cpu().numpy().astype(np.float64)
+        res[name]["llg_100_steps_64x64x8_max_abs_vs_fp64_oracle"] = float(np.abs(got - want).max())
+        mesh.close()
+    return res
+
+
 def run_reference(args):
     rank, world, local = _dist_env()
     if rank != 0:
@@ -451,7 +532,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--llg-steps", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="film", choices=["film", "batch", "serve"])
+    ap.add_argument("--workload", default="film", choices=["film", "batch", "serve", "3d"])
+    ap.add_argument("--oracle-3d", action="store_true", help="3d: FP64 oracle of the full mesh (minutes, ~30 GB)")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--rate", type=float, default=200.0)
@@ -464,6 +546,8 @@ def main():
         res = run_batch(args)
     elif args.workload == "serve":
         res = run_serve(args)
+    elif args.workload == "3d":
+        res = run_3d(args)
     else:
         res = run_ours(args)
     if res is not None:

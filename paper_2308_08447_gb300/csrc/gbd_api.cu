@@ -132,8 +132,10 @@ static gbd_status check_desc(const gbd_mesh_desc* d, gbd::Plan& p) {
   if (!(d->gamma >= 0) || !std::isfinite(d->gamma)) return fail(GBD_EINVAL, "gamma must be finite and >= 0");
   for (int i = 0; i < 3; ++i)
     if (!std::isfinite(d->Hext[i])) return fail(GBD_EINVAL, "Hext must be finite");
-  if (d->precision != GBD_FP32) return fail(GBD_EUNSUPPORTED, "only GBD_FP32 meshes are built by gbd_mesh_create");
+  if (d->precision != GBD_FP32 && d->precision != GBD_SPLIT_BF16)
+    return fail(GBD_EUNSUPPORTED, "precision must be GBD_FP32 or GBD_SPLIT_BF16");
   if (!gbd::make_plan(d->nx, d->ny, d->nz, p, &why)) return fail(GBD_EUNSUPPORTED, why);
+  p.prec = (d->precision == GBD_SPLIT_BF16) ? 1 : 0;
   return GBD_OK;
 }
 
@@ -210,7 +212,7 @@ static void enqueue_conv(gbd_mesh* m, cudaStream_t st) {
   if (p.film) {
     a.dst = m->S;
     a.Kf = static_cast<const float4*>(m->K);
-    timed(m, GBD_PASS_FILM_CONV, st, [&] { gbd::launch_film_conv(m->p.var_film, a, m->tw, st); });
+    timed(m, GBD_PASS_FILM_CONV, st, [&] { gbd::launch_film_conv(m->p.var_film, m->p.prec, a, m->tw, st); });
     return;
   }
   a.K3 = static_cast<const float*>(m->K);
@@ -218,19 +220,19 @@ static void enqueue_conv(gbd_mesh* m, cudaStream_t st) {
     a.lines_total = 3LL * p.nz * p.Hx;
     a.src = m->S;
     a.dst = m->T;
-    timed(m, GBD_PASS_Y_FWD, st, [&] { gbd::launch_y_fwd(m->p.var_y, a, m->tw, st); });
+    timed(m, GBD_PASS_Y_FWD, st, [&] { gbd::launch_y_fwd(m->p.var_y, m->p.prec, a, m->tw, st); });
     a.dst = m->T;
     a.Q = (long long)p.Hx * p.Py;
     a.Pyq = p.Py;
-    timed(m, GBD_PASS_Z_CONV, st, [&] { gbd::launch_z_conv(m->p.var_z, a, m->tw, st); });
+    timed(m, GBD_PASS_Z_CONV, st, [&] { gbd::launch_z_conv(m->p.var_z, m->p.prec, a, m->tw, st); });
     a.src = m->T;
     a.dst = m->S;
-    timed(m, GBD_PASS_Y_INV, st, [&] { gbd::launch_y_inv(m->p.var_y, a, m->tw, st); });
+    timed(m, GBD_PASS_Y_INV, st, [&] { gbd::launch_y_inv(m->p.var_y, m->p.prec, a, m->tw, st); });
   } else {
     a.dst = m->S;
     a.Q = p.Hx;
     a.Pyq = 1;
-    timed(m, GBD_PASS_Z_CONV, st, [&] { gbd::launch_z_conv(m->p.var_z, a, m->tw, st); });
+    timed(m, GBD_PASS_Z_CONV, st, [&] { gbd::launch_z_conv(m->p.var_z, m->p.prec, a, m->tw, st); });
   }
 }
 
@@ -335,12 +337,12 @@ gbd_status gbd_mesh_create(const gbd_mesh_desc* desc, gbd_mesh** out) {
   }
   // shared-memory attributes of this mesh's kernels (both tile variants), set now so that
   // later launches, also inside a stream capture, need no configuration call
-  gbd::prepare_row(p.Lx);
+  gbd::prepare_row(p.Lx, p.prec);
   if (p.film) {
-    gbd::prepare_film_conv(p.Py);
+    gbd::prepare_film_conv(p.Py, p.prec);
   } else {
-    gbd::prepare_z_conv(p.Pz);
-    if (p.ny > 1) gbd::prepare_y_passes(p.Py);
+    gbd::prepare_z_conv(p.Pz, p.prec);
+    if (p.ny > 1) gbd::prepare_y_passes(p.Py, p.prec);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -504,13 +506,13 @@ gbd_status gbd_demag(gbd_mesh* m, const float* M, float* H, void* stream) {
   a.in = M;
   a.mode = gbd::ROW_FWD;
   a.fwd_after = 1;
-  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, a, m->tw, st); });
+  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
   enqueue_conv(m, st);
   a.hscale = 1.f;
   a.out = H;
   a.mode = gbd::ROW_H;
   a.fwd_after = 0;
-  timed(m, GBD_PASS_ROW_INV, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, a, m->tw, st); });
+  timed(m, GBD_PASS_ROW_INV, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
   return after_launch("gbd_demag");
 }
 
@@ -523,13 +525,13 @@ static gbd_status field_like(gbd_mesh* m, const float* mm, float* out, int mode,
   a.in = mm;
   a.mode = gbd::ROW_FWD;
   a.fwd_after = 1;
-  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, a, m->tw, st); });
+  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
   enqueue_conv(m, st);
   a.ms = mm;
   a.out = out;
   a.mode = mode;
   a.fwd_after = 0;
-  timed(m, GBD_PASS_ROW_INV, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, a, m->tw, st); });
+  timed(m, GBD_PASS_ROW_INV, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
   return after_launch(name);
 }
 
@@ -554,7 +556,7 @@ gbd_status gbd_llg_step(gbd_mesh* m, float* mm, int nsteps, double dt, void* str
   a.in = mm;
   a.mode = gbd::ROW_FWD;
   a.fwd_after = 1;
-  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, a, m->tw, st); });
+  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
   a.m0 = mm;
   a.m0_out = mm;
   a.acc = m->acc;
@@ -569,7 +571,7 @@ gbd_status gbd_llg_step(gbd_mesh* m, float* mm, int nsteps, double dt, void* str
       a.mnext = mn[stage];
       a.mode = gbd::ROW_RK1 + stage;
       a.fwd_after = (last && stage == 3) ? 0 : 1;
-      timed(m, GBD_PASS_ROW_RK, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, a, m->tw, st); });
+      timed(m, GBD_PASS_ROW_RK, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
     }
   }
   return after_launch("gbd_llg_step");
@@ -598,7 +600,7 @@ void enqueue_conv_on(const gbd_mesh* m, float2* S, float2* T, cudaStream_t st) {
   if (p.film) {
     a.dst = S;
     a.Kf = static_cast<const float4*>(m->K);
-    gbd::launch_film_conv(m->p.var_film, a, m->tw, st);
+    gbd::launch_film_conv(m->p.var_film, m->p.prec, a, m->tw, st);
     return;
   }
   a.K3 = static_cast<const float*>(m->K);
@@ -606,18 +608,18 @@ void enqueue_conv_on(const gbd_mesh* m, float2* S, float2* T, cudaStream_t st) {
     a.lines_total = 3LL * p.nz * p.Hx;
     a.src = S;
     a.dst = T;
-    gbd::launch_y_fwd(m->p.var_y, a, m->tw, st);
+    gbd::launch_y_fwd(m->p.var_y, m->p.prec, a, m->tw, st);
     a.Q = (long long)p.Hx * p.Py;
     a.Pyq = p.Py;
-    gbd::launch_z_conv(m->p.var_z, a, m->tw, st);
+    gbd::launch_z_conv(m->p.var_z, m->p.prec, a, m->tw, st);
     a.src = T;
     a.dst = S;
-    gbd::launch_y_inv(m->p.var_y, a, m->tw, st);
+    gbd::launch_y_inv(m->p.var_y, m->p.prec, a, m->tw, st);
   } else {
     a.dst = S;
     a.Q = p.Hx;
     a.Pyq = 1;
-    gbd::launch_z_conv(m->p.var_z, a, m->tw, st);
+    gbd::launch_z_conv(m->p.var_z, m->p.prec, a, m->tw, st);
   }
 }
 }  // namespace
@@ -654,13 +656,13 @@ extern "C" gbd_status gbd_demag_noalloc(gbd_mesh* m, const float* M, float* H, v
   a.in = M;
   a.mode = gbd::ROW_FWD;
   a.fwd_after = 1;
-  gbd::launch_row(p.Lx, p.var_row, a, m->tw, st);
+  gbd::launch_row(p.Lx, p.var_row, p.prec, a, m->tw, st);
   enqueue_conv_on(m, S, T, st);
   a.hscale = 1.f;
   a.out = H;
   a.mode = gbd::ROW_H;
   a.fwd_after = 0;
-  gbd::launch_row(p.Lx, p.var_row, a, m->tw, st);
+  gbd::launch_row(p.Lx, p.var_row, p.prec, a, m->tw, st);
   return after_launch("gbd_demag_noalloc");
 }
 
@@ -822,12 +824,12 @@ extern "C" gbd_status gbd_mesh_autotune(gbd_mesh* m, void* stream) {
   ra.acc = m->acc;
   ra.mode = gbd::ROW_RK2;
   ra.fwd_after = 1;
-  e = pick(0, [&](int v) { gbd::launch_row(p.Lx, v, ra, m->tw, st); });
+  e = pick(0, [&](int v) { gbd::launch_row(p.Lx, v, p.prec, ra, m->tw, st); });
   gbd::ColArgs ca = col_args(m);
   if (e == cudaSuccess && p.film) {
     ca.dst = m->S;
     ca.Kf = static_cast<const float4*>(m->K);
-    e = pick(1, [&](int v) { gbd::launch_film_conv(v, ca, m->tw, st); });
+    e = pick(1, [&](int v) { gbd::launch_film_conv(v, p.prec, ca, m->tw, st); });
   } else if (e == cudaSuccess) {
     ca.K3 = static_cast<const float*>(m->K);
     if (p.ny > 1) {
@@ -835,11 +837,11 @@ extern "C" gbd_status gbd_mesh_autotune(gbd_mesh* m, void* stream) {
       ca.src = m->S;
       ca.dst = m->T;
       e = pick(2, [&](int v) {
-        gbd::launch_y_fwd(v, ca, m->tw, st);
+        gbd::launch_y_fwd(v, p.prec, ca, m->tw, st);
         gbd::ColArgs cb = ca;
         cb.src = m->T;
         cb.dst = m->S;
-        gbd::launch_y_inv(v, cb, m->tw, st);
+        gbd::launch_y_inv(v, p.prec, cb, m->tw, st);
       });
       ca.dst = m->T;
       ca.Q = (long long)p.Hx * p.Py;
@@ -849,7 +851,7 @@ extern "C" gbd_status gbd_mesh_autotune(gbd_mesh* m, void* stream) {
       ca.Q = p.Hx;
       ca.Pyq = 1;
     }
-    if (e == cudaSuccess) e = pick(3, [&](int v) { gbd::launch_z_conv(v, ca, m->tw, st); });
+    if (e == cudaSuccess) e = pick(3, [&](int v) { gbd::launch_z_conv(v, p.prec, ca, m->tw, st); });
   }
   if (e != cudaSuccess) return cuda_fail(e, "gbd_mesh_autotune");
   apply_tuning(m, best);
@@ -895,7 +897,7 @@ void enqueue_llg(gbd_mesh* m, float* mm, int nsteps, double dt, cudaStream_t st)
   a.in = mm;
   a.mode = gbd::ROW_FWD;
   a.fwd_after = 1;
-  gbd::launch_row(m->p.Lx, m->p.var_row, a, m->tw, st);
+  gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st);
   a.m0 = mm;
   a.m0_out = mm;
   a.acc = m->acc;
@@ -912,7 +914,7 @@ void enqueue_llg(gbd_mesh* m, float* mm, int nsteps, double dt, cudaStream_t st)
       a.mnext = mn[stage];
       a.mode = gbd::ROW_RK1 + stage;
       a.fwd_after = (last && stage == 3) ? 0 : 1;
-      gbd::launch_row(m->p.Lx, m->p.var_row, a, m->tw, st);
+      gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st);
     }
   }
 }

@@ -40,7 +40,7 @@ __device__ __forceinline__ void fused_item(int line0, int lstride, int j, const 
 }
 
 // film: one block = C columns kx, three components each, lines = c * C + cc.
-template <int L, int C_>
+template <int L, int C_, int PREC>
 __global__ void __launch_bounds__(3 * C_ * L / GBD_E, min_blocks(3 * C_ * L / GBD_E))
     film_conv_kernel(ColArgs a, const float2* __restrict__ tw) {
   constexpr int C = C_;
@@ -94,19 +94,19 @@ __global__ void __launch_bounds__(3 * C_ * L / GBD_E, min_blocks(3 * C_ * L / GB
   if constexpr (NP <= 1) {
     run_fused(gld, gst);
   } else {
-    stockham_pass<-1, false, L, radix_at(L, true, 0), 1, LINES, false, false>(tw, gld, sst);
+    pass_any<PREC, -1, false, L, radix_at(L, true, 0), 1, LINES, false, false>(tw, gld, sst);
     __syncthreads();
-    fwd_passes_smem<-1, L, true, LINES, false, LS, 1, NP - 1>(sm, tw);
+    fwd_passes_smem<-1, L, true, LINES, false, LS, 1, NP - 1, PREC>(sm, tw);
     run_fused(sld, sst);
     __syncthreads();
-    adj_passes_smem<1, L, true, LINES, false, LS, NP - 1, 1>(sm, tw);
-    stockham_pass<1, true, L, radix_at(L, true, 0), 1, LINES, false, false>(tw, sld, gst);
+    adj_passes_smem<1, L, true, LINES, false, LS, NP - 1, 1, PREC>(sm, tw);
+    pass_any<PREC, 1, true, L, radix_at(L, true, 0), 1, LINES, false, false>(tw, sld, gst);
   }
 }
 
 // 3D y passes over independent lines l = (c*nz + z)*Hx + kx: forward S (ny) -> T (Py),
 // inverse T (Py) -> S (first ny).
-template <int L, int W_>
+template <int L, int W_, int PREC>
 __global__ void __launch_bounds__(3 * W_ * L / GBD_E, min_blocks(3 * W_ * L / GBD_E))
     z_conv_kernel(ColArgs a, const float2* __restrict__ tw) {
   constexpr int W = W_;
@@ -174,13 +174,13 @@ __global__ void __launch_bounds__(3 * W_ * L / GBD_E, min_blocks(3 * W_ * L / GB
   if constexpr (NP == 1) {
     run_fused(gld, gst);
   } else {
-    stockham_pass<-1, false, L, radix_at(L, true, 0), 1, LINES, true, false>(tw, gld, sst);
+    pass_any<PREC, -1, false, L, radix_at(L, true, 0), 1, LINES, true, false>(tw, gld, sst);
     __syncthreads();
-    fwd_passes_smem<-1, L, true, LINES, true, LS, 1, NP - 1>(sm, tw);
+    fwd_passes_smem<-1, L, true, LINES, true, LS, 1, NP - 1, PREC>(sm, tw);
     run_fused(sld, sst);
     __syncthreads();
-    adj_passes_smem<1, L, true, LINES, true, LS, NP - 1, 1>(sm, tw);
-    stockham_pass<1, true, L, radix_at(L, true, 0), 1, LINES, true, false>(tw, sld, gst);
+    adj_passes_smem<1, L, true, LINES, true, LS, NP - 1, 1, PREC>(sm, tw);
+    pass_any<PREC, 1, true, L, radix_at(L, true, 0), 1, LINES, true, false>(tw, sld, gst);
   }
 }
 
@@ -188,31 +188,43 @@ __global__ void __launch_bounds__(3 * W_ * L / GBD_E, min_blocks(3 * W_ * L / GB
 // ---- launchers -------------------------------------------------------------------------------
 
 // a == nullptr only prepares the kernel (shared-memory attribute), without a launch.
-template <int L, int C>
+template <int L, int C, int PREC>
 static void film_launch_t(const ColArgs* a, const float2* tw, cudaStream_t st) {
   constexpr int T = 3 * C * L / GBD_E;
   const size_t smem = (size_t)3 * C * line_stride<L, false>() * sizeof(float2);
-  prep(film_conv_kernel<L, C>, smem);
-  if (a) film_conv_kernel<L, C><<<(a->Hx + C - 1) / C, T, smem, st>>>(*a, tw);
+  prep(film_conv_kernel<L, C, PREC>, smem);
+  if (a) film_conv_kernel<L, C, PREC><<<(a->Hx + C - 1) / C, T, smem, st>>>(*a, tw);
 }
 
-template <int L, int W>
+template <int L, int W, int PREC>
 static void zconv_launch_t(const ColArgs* a, const float2* tw, cudaStream_t st) {
   constexpr int T = 3 * W * L / GBD_E;
   const size_t smem = (size_t)3 * W * line_stride<L, true>() * sizeof(float2);
-  prep(z_conv_kernel<L, W>, smem);
-  if (a) z_conv_kernel<L, W><<<(unsigned)((a->Q + W - 1) / W), T, smem, st>>>(*a, tw);
+  prep(z_conv_kernel<L, W, PREC>, smem);
+  if (a) z_conv_kernel<L, W, PREC><<<(unsigned)((a->Q + W - 1) / W), T, smem, st>>>(*a, tw);
+}
+
+// prec < 0 (with a == nullptr) prepares both precisions
+template <int L, int C>
+static void film_launch_p(int prec, const ColArgs* a, const float2* tw, cudaStream_t st) {
+  if (prec <= 0) film_launch_t<L, C, 0>(a, tw, st);
+  if (prec != 0) film_launch_t<L, C, 1>(a, tw, st);
+}
+template <int L, int W>
+static void zconv_launch_p(int prec, const ColArgs* a, const float2* tw, cudaStream_t st) {
+  if (prec <= 0) zconv_launch_t<L, W, 0>(a, tw, st);
+  if (prec != 0) zconv_launch_t<L, W, 1>(a, tw, st);
 }
 
 #define GBD_FILM_CASE(L)                                          \
   case L:                                                         \
     if (var <= 0)                                                 \
-      film_launch_t<L, film_cols(L, 0)>(a, tw, st);               \
+      film_launch_p<L, film_cols(L, 0)>(prec, a, tw, st);               \
     if (var != 0)                                                 \
-      film_launch_t<L, film_cols(L, 1)>(a, tw, st);               \
+      film_launch_p<L, film_cols(L, 1)>(prec, a, tw, st);               \
     return true;
 
-static bool film_dispatch(int Py, int var, const ColArgs* a, const float2* tw, cudaStream_t st) {
+static bool film_dispatch(int Py, int var, int prec, const ColArgs* a, const float2* tw, cudaStream_t st) {
   switch (Py) {
     GBD_FILM_CASE(1)
     GBD_FILM_CASE(4)
@@ -230,20 +242,20 @@ static bool film_dispatch(int Py, int var, const ColArgs* a, const float2* tw, c
   }
 }
 
-bool launch_film_conv(int var, const ColArgs& a, const float2* tw, cudaStream_t st) {
-  return film_dispatch(a.Py, var, &a, tw, st);
+bool launch_film_conv(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st) {
+  return film_dispatch(a.Py, var, prec, &a, tw, st);
 }
-bool prepare_film_conv(int Py) { return film_dispatch(Py, -1, nullptr, nullptr, nullptr); }
+bool prepare_film_conv(int Py, int prec) { return film_dispatch(Py, -1, prec, nullptr, nullptr, nullptr); }
 
 #define GBD_Z_CASE(L)                                             \
   case L:                                                         \
     if (var <= 0)                                                 \
-      zconv_launch_t<L, zconv_cols(L, 0)>(a, tw, st);             \
+      zconv_launch_p<L, zconv_cols(L, 0)>(prec, a, tw, st);             \
     if (var != 0)                                                 \
-      zconv_launch_t<L, zconv_cols(L, 1)>(a, tw, st);             \
+      zconv_launch_p<L, zconv_cols(L, 1)>(prec, a, tw, st);             \
     return true;
 
-static bool z_dispatch(int Pz, int var, const ColArgs* a, const float2* tw, cudaStream_t st) {
+static bool z_dispatch(int Pz, int var, int prec, const ColArgs* a, const float2* tw, cudaStream_t st) {
   switch (Pz) {
     GBD_Z_CASE(4)
     GBD_Z_CASE(8)
@@ -260,9 +272,9 @@ static bool z_dispatch(int Pz, int var, const ColArgs* a, const float2* tw, cuda
   }
 }
 
-bool launch_z_conv(int var, const ColArgs& a, const float2* tw, cudaStream_t st) {
-  return z_dispatch(a.Pz, var, &a, tw, st);
+bool launch_z_conv(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st) {
+  return z_dispatch(a.Pz, var, prec, &a, tw, st);
 }
-bool prepare_z_conv(int Pz) { return z_dispatch(Pz, -1, nullptr, nullptr, nullptr); }
+bool prepare_z_conv(int Pz, int prec) { return z_dispatch(Pz, -1, prec, nullptr, nullptr, nullptr); }
 
 }  // namespace gbd

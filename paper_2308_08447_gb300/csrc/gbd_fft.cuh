@@ -302,29 +302,5 @@ __device__ __forceinline__ void stockham_pass_sm(float2* sm, const float2* __res
   }
 }
 
-// Passes [P, PEND) of the forward chain (sign S) in place in shared memory; LS is the
-// caller's line stride in float2 units.
-template <int S, int L, bool CONV, int LINES, bool LF, int LS, int P, int PEND>
-__device__ __forceinline__ void fwd_passes_smem(float2* sm, const float2* __restrict__ tw) {
-  if constexpr (P < PEND) {
-    constexpr int R = radix_at(L, CONV, P);
-    constexpr int Ns = ns_at(L, CONV, P);
-    stockham_pass_sm<S, false, L, R, Ns, LINES, LF, LS>(sm, tw);
-    __syncthreads();
-    fwd_passes_smem<S, L, CONV, LINES, LF, LS, P + 1, PEND>(sm, tw);
-  }
-}
-
-// Adjoint passes P-1 down to PEND (inclusive) in place in shared memory.
-template <int S, int L, bool CONV, int LINES, bool LF, int LS, int P, int PEND>
-__device__ __forceinline__ void adj_passes_smem(float2* sm, const float2* __restrict__ tw) {
-  if constexpr (P > PEND) {
-    constexpr int R = radix_at(L, CONV, P - 1);
-    constexpr int Ns = ns_at(L, CONV, P - 1);
-    stockham_pass_sm<S, true, L, R, Ns, LINES, LF, LS>(sm, tw);
-    __syncthreads();
-    adj_passes_smem<S, L, CONV, LINES, LF, LS, P - 1, PEND>(sm, tw);
-  }
-}
 
 }  // namespace gbd

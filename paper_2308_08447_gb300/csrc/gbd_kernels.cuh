@@ -82,18 +82,19 @@ struct ColArgs {
 
 // Launchers dispatch on the transform length (a power of two) and the tile variant; they
 // return false for a length without an instantiation.
-bool launch_row(int Lx, int var, const RowArgs& a, const float2* tw, cudaStream_t st);
-bool launch_film_conv(int var, const ColArgs& a, const float2* tw, cudaStream_t st);
-bool launch_y_fwd(int var, const ColArgs& a, const float2* tw, cudaStream_t st);
-bool launch_y_inv(int var, const ColArgs& a, const float2* tw, cudaStream_t st);
-bool launch_z_conv(int var, const ColArgs& a, const float2* tw, cudaStream_t st);
+// prec: 0 FP32 stages; 1 radix-16 stages on the tensor cores in split BF16 (gbd_tc.cuh).
+bool launch_row(int Lx, int var, int prec, const RowArgs& a, const float2* tw, cudaStream_t st);
+bool launch_film_conv(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st);
+bool launch_y_fwd(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st);
+bool launch_y_inv(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st);
+bool launch_z_conv(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st);
 
 // Set the kernels' shared-memory attribute for both variants of a length without launching
 // (done when a mesh is created, so later launches inside a stream capture need no driver
 // configuration call). Return false for a length without an instantiation.
-bool prepare_row(int Lx);
-bool prepare_film_conv(int Py);
-bool prepare_y_passes(int Py);
-bool prepare_z_conv(int Pz);
+bool prepare_row(int Lx, int prec);
+bool prepare_film_conv(int Py, int prec);
+bool prepare_y_passes(int Py, int prec);
+bool prepare_z_conv(int Pz, int prec);
 
 }  // namespace gbd

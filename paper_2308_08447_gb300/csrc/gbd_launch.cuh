@@ -2,7 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
-#include "gbd_fft.cuh"
+#include "gbd_tc.cuh"
 #include "gbd_kernels.cuh"
 
 namespace gbd {

@@ -23,6 +23,8 @@ struct Plan {
   // tile variants (0 / 1) per kernel family, set by the autotuner, and the block shapes
   // they give
   int var_row = 1, var_film = 0, var_y = 0, var_z = 0;
+  // arithmetic of the radix-16 FFT stages: 0 FP32, 1 split BF16 on the tensor cores
+  int prec = 0;
   int RB = 1;           // rows per x-row block
   int Cf = 1;           // columns per film-conv block
   int Cy = 1;           // lines per y-pass block

@@ -27,7 +27,7 @@ bool prep_seen(const void* k, int dev) {
 // inverse, and the forward reads only those: the upper half is the zero padding.
 // ---------------------------------------------------------------------------------------------
 
-template <int LX, int RB_>
+template <int LX, int RB_, int PREC>
 __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX / GBD_E))
     row_kernel(RowArgs a, const float2* __restrict__ tw) {
   constexpr int RB = RB_;
@@ -131,12 +131,12 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
     __syncthreads();
     // 2. unnormalised inverse FFT: adjoint passes, the last one keeping the lower half only.
     if constexpr (NP >= 1) {
-      adj_passes_smem<1, LX, false, LINES, false, LS, NP, 1>(sm, tw);
+      adj_passes_smem<1, LX, false, LINES, false, LS, NP, 1, PREC>(sm, tw);
       auto ld = [&](int line, int i) { return sm[line * LS + pad(i)]; };
       auto st = [&](int line, int i, float2 v) {
         if (i < HALF) sm[line * LS + pad(i)] = v;
       };
-      stockham_pass<1, true, LX, radix_at(LX, false, 0), 1, LINES, false, true>(tw, ld, st);
+      pass_any<PREC, 1, true, LX, radix_at(LX, false, 0), 1, LINES, false, true>(tw, ld, st);
       __syncthreads();
     }
     // 3. epilogue on the real rows: float view of line position x is 2 pad(x/2) + (x & 1).
@@ -376,9 +376,9 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
   if constexpr (NP >= 1) {
     auto ld = [&](int line, int i) { return i < HALF ? sm[line * LS + pad(i)] : make_float2(0.f, 0.f); };
     auto st = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
-    stockham_pass<-1, false, LX, radix_at(LX, false, 0), 1, LINES, false, true>(tw, ld, st);
+    pass_any<PREC, -1, false, LX, radix_at(LX, false, 0), 1, LINES, false, true>(tw, ld, st);
     __syncthreads();
-    fwd_passes_smem<-1, LX, false, LINES, false, LS, 1, NP>(sm, tw);
+    fwd_passes_smem<-1, LX, false, LINES, false, LS, 1, NP, PREC>(sm, tw);
   }
   // 6. Z -> X pairwise and store the half spectrum, VR adjacent rows per item.
   for (int e = threadIdx.x; e < RG * 3 * (HALF + 1); e += T) {
@@ -427,24 +427,31 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
 
 // ---- launcher --------------------------------------------------------------------------------
 
-template <int LX, int RB>
+template <int LX, int RB, int PREC>
 static void row_launch_t(const RowArgs* a, const float2* tw, cudaStream_t st) {
   constexpr int T = 3 * RB * LX / GBD_E;
   const size_t smem = (size_t)3 * RB * line_stride<LX, true>() * sizeof(float2);
-  prep(row_kernel<LX, RB>, smem);
-  if (a) row_kernel<LX, RB><<<(a->rows + RB - 1) / RB, T, smem, st>>>(*a, tw);
+  prep(row_kernel<LX, RB, PREC>, smem);
+  if (a) row_kernel<LX, RB, PREC><<<(a->rows + RB - 1) / RB, T, smem, st>>>(*a, tw);
+}
+
+// prec < 0 (with a == nullptr) prepares both precisions
+template <int LX, int RB>
+static void row_launch_p(int prec, const RowArgs* a, const float2* tw, cudaStream_t st) {
+  if (prec <= 0) row_launch_t<LX, RB, 0>(a, tw, st);
+  if (prec != 0) row_launch_t<LX, RB, 1>(a, tw, st);
 }
 
 #define GBD_ROW_CASE(LX)                                        \
   case LX:                                                      \
     if (var <= 0)                                               \
-      row_launch_t<LX, row_rb(LX, 0)>(a, tw, st);               \
+      row_launch_p<LX, row_rb(LX, 0)>(prec, a, tw, st);               \
     if (var != 0)                                               \
-      row_launch_t<LX, row_rb(LX, 1)>(a, tw, st);               \
+      row_launch_p<LX, row_rb(LX, 1)>(prec, a, tw, st);               \
     return true;
 
 // a == nullptr only prepares the kernels (both variants when var < 0).
-static bool row_dispatch(int Lx, int var, const RowArgs* a, const float2* tw, cudaStream_t st) {
+static bool row_dispatch(int Lx, int var, int prec, const RowArgs* a, const float2* tw, cudaStream_t st) {
   switch (Lx) {
     GBD_ROW_CASE(1)
     GBD_ROW_CASE(2)
@@ -463,9 +470,9 @@ static bool row_dispatch(int Lx, int var, const RowArgs* a, const float2* tw, cu
   }
 }
 
-bool launch_row(int Lx, int var, const RowArgs& a, const float2* tw, cudaStream_t st) {
-  return row_dispatch(Lx, var, &a, tw, st);
+bool launch_row(int Lx, int var, int prec, const RowArgs& a, const float2* tw, cudaStream_t st) {
+  return row_dispatch(Lx, var, prec, &a, tw, st);
 }
-bool prepare_row(int Lx) { return row_dispatch(Lx, -1, nullptr, nullptr, nullptr); }
+bool prepare_row(int Lx, int prec) { return row_dispatch(Lx, -1, prec, nullptr, nullptr, nullptr); }
 
 }  // namespace gbd

@@ -1,0 +1,212 @@
+// Radix-16 Stockham pass with the 16-point DFT on the tensor cores, split BF16 (hi + lo) with
+// FP32 accumulation -- the optional precision variant of the FFT stages.
+//
+// A butterfly's DFT is the real 32 x 32 product  [Yr; Yi] = [C, -sS; sS, C] [Xr; Xi]  with
+// C_qr = cos(2 pi q r / 16), S_qr = sin(2 pi q r / 16) and s the transform sign. Both operands
+// are split, A = Ah + Al and X = Xh + Xl with Ah = bf16(A), Al = bf16(A - Ah) (likewise X), and
+// Y ~= Ah Xh + Ah Xl + Al Xh in FP32 (the dropped Al Xl is below 2^-16 of the terms); the
+// representation error of each operand is about 2^-16 relative, the Sec. II rule of halving
+// precision "with normalization" needs no scale here because BF16 keeps FP32's exponent range.
+//
+// mma.sync.m16n8k16 (BF16 in, FP32 accumulate): a warp takes 8 butterflies (the n = 8 columns)
+// per group and 4 groups per pass, the same 32 butterflies its threads take in the FP32 pass.
+// With g = lane / 4 and t = lane % 4, lane holds for butterfly n = g the inputs r in
+// {2t, 2t+1, 2t+8, 2t+9} (B fragment rows: k-tile 0 = real parts, k-tile 1 = imaginary parts)
+// and receives the outputs q in {g, g+8} of butterflies {2t, 2t+1} (C fragment, m-tile 0 =
+// real parts, m-tile 1 = imaginary parts). Twiddles stay in FP32: applied to the inputs in a
+// forward pass and to the outputs in an adjoint pass, exactly as in the FP32 pass.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "gbd_fft.cuh"
+
+namespace gbd {
+
+// bits of a bfloat16x2 with lo in the low half
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<unsigned*>(&v);
+}
+
+// x = hi + lo in bf16 pairs: (a, b) -> hi bits, lo bits
+__device__ __forceinline__ void split2(float a, float b, unsigned& hi, unsigned& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float ra = a - __bfloat162float(h.x);
+  const float rb = b - __bfloat162float(h.y);
+  hi = *reinterpret_cast<const unsigned*>(&h);
+  lo = pack_bf16(ra, rb);
+}
+
+__device__ __forceinline__ void mma_bf16(float* d, const unsigned* a, unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// cos / sin of pi m / 8, m in [0, 16)
+__device__ __forceinline__ float cos16(int m) {
+  const float c[16] = {1.0f, 0.92387953251128675613f, 0.70710678118654752440f, 0.38268343236508977173f,
+                       0.0f, -0.38268343236508977173f, -0.70710678118654752440f, -0.92387953251128675613f,
+                       -1.0f, -0.92387953251128675613f, -0.70710678118654752440f, -0.38268343236508977173f,
+                       0.0f, 0.38268343236508977173f, 0.70710678118654752440f, 0.92387953251128675613f};
+  return c[m & 15];
+}
+__device__ __forceinline__ float sin16(int m) { return cos16(m - 4); }
+
+// Element (row, col) of the real 32 x 32 DFT-16 matrix for sign S: rows 0..15 give Re Y_q,
+// rows 16..31 Im Y_q; cols 0..15 take Re X_r, cols 16..31 Im X_r.
+template <int S>
+__device__ __forceinline__ float dft16_real(int row, int col) {
+  const int q = row & 15, r = col & 15;
+  const int m = (q * r) & 15;  // angle 2 pi q r / 16 = pi m / 8
+  const float c = cos16(m), s = S * sin16(m);
+  if (row < 16) return col < 16 ? c : -s;
+  return col < 16 ? s : c;
+}
+
+// A fragments of the split matrix: frag[mt][kt][hi/lo][4 registers]
+template <int S>
+struct Dft16Frags {
+  unsigned f[2][2][2][4];
+  __device__ __forceinline__ void build(int lane) {
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int kt = 0; kt < 2; ++kt) {
+        const int r0 = mt * 16 + g, c0 = kt * 16 + 2 * t;
+        const float v[8] = {dft16_real<S>(r0, c0), dft16_real<S>(r0, c0 + 1),
+                            dft16_real<S>(r0 + 8, c0), dft16_real<S>(r0 + 8, c0 + 1),
+                            dft16_real<S>(r0, c0 + 8), dft16_real<S>(r0, c0 + 9),
+                            dft16_real<S>(r0 + 8, c0 + 8), dft16_real<S>(r0 + 8, c0 + 9)};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) split2(v[2 * i], v[2 * i + 1], f[mt][kt][0][i], f[mt][kt][1][i]);
+      }
+  }
+};
+
+// Radix-16 pass (forward: loads j + r L/16, stores (j-k) 16 + k + q Ns; adjoint: reverse),
+// block of exactly LINES * L / 16 threads, like stockham_pass.
+template <int S, bool ADJ, int L, int Ns, int LINES, bool LF, bool SYNC_MID, class LD, class ST>
+__device__ __forceinline__ void stockham_pass_tc(const float2* __restrict__ tw, LD ld, ST st) {
+  constexpr int R = 16;
+  constexpr int LR = L / R;
+  constexpr int step = GBD_TW_LEN / (Ns * R);
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int rin[4] = {2 * t, 2 * t + 1, 2 * t + 8, 2 * t + 9};
+  auto map = [&](int b, int& line, int& j) {
+    if (LF) {
+      line = b % LINES;
+      j = b / LINES;
+    } else {
+      line = b / LR;
+      j = b % LR;
+    }
+  };
+  // loads: 4 groups of 8 butterflies, 4 inputs each
+  float2 x[4][4];
+#pragma unroll
+  for (int grp = 0; grp < 4; ++grp) {
+    int line, j;
+    map(warp * 32 + grp * 8 + g, line, j);
+    const int k = j % Ns;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = rin[i];
+      float2 v = ld(line, ADJ ? (j - k) * R + k + r * Ns : j + r * LR);
+      if (!ADJ && Ns > 1 && r > 0) v = cmul(v, twiddle<S>(tw, r * k * step));
+      x[grp][i] = v;
+    }
+  }
+  if (SYNC_MID) __syncthreads();
+  Dft16Frags<S> A;
+  A.build(lane);
+#pragma unroll
+  for (int grp = 0; grp < 4; ++grp) {
+    // B fragments: k-tile 0 real parts, k-tile 1 imaginary parts; rows (r) 2t, 2t+1 | 2t+8, 2t+9
+    unsigned bh[2][2], bl[2][2];
+    split2(x[grp][0].x, x[grp][1].x, bh[0][0], bl[0][0]);
+    split2(x[grp][2].x, x[grp][3].x, bh[0][1], bl[0][1]);
+    split2(x[grp][0].y, x[grp][1].y, bh[1][0], bl[1][0]);
+    split2(x[grp][2].y, x[grp][3].y, bh[1][1], bl[1][1]);
+    float y[2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) y[mt][i] = 0.f;
+#pragma unroll
+      for (int kt = 0; kt < 2; ++kt) {
+        mma_bf16(y[mt], A.f[mt][kt][1], bh[kt][0], bh[kt][1]);   // Al Xh
+        mma_bf16(y[mt], A.f[mt][kt][0], bl[kt][0], bl[kt][1]);   // Ah Xl
+        mma_bf16(y[mt], A.f[mt][kt][0], bh[kt][0], bh[kt][1]);   // Ah Xh
+      }
+    }
+    // outputs: q in {g, g+8} of butterflies n in {2t, 2t+1}: (Re, Im) = (y[0][.], y[1][.])
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      int line, j;
+      map(warp * 32 + grp * 8 + 2 * t + c, line, j);
+      const int k = j % Ns;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int q = g + 8 * h;
+        float2 v = make_float2(y[0][2 * h + c], y[1][2 * h + c]);
+        if (ADJ && Ns > 1 && q > 0) v = cmul(v, twiddle<S>(tw, q * k * step));
+        st(line, ADJ ? j + q * LR : (j - k) * R + k + q * Ns, v);
+      }
+    }
+  }
+}
+
+// ---- pass selection by precision -------------------------------------------------------------
+// PREC = 0: FP32 everywhere. PREC = 1: every radix-16 pass on the tensor cores (split BF16).
+
+template <int PREC, int S, bool ADJ, int L, int R, int Ns, int LINES, bool LF, bool SYNC_MID, class LD, class ST>
+__device__ __forceinline__ void pass_any(const float2* __restrict__ tw, LD ld, ST st) {
+  if constexpr (PREC != 0 && R == 16)
+    stockham_pass_tc<S, ADJ, L, Ns, LINES, LF, SYNC_MID>(tw, ld, st);
+  else
+    stockham_pass<S, ADJ, L, R, Ns, LINES, LF, SYNC_MID>(tw, ld, st);
+}
+
+template <int PREC, int S, bool ADJ, int L, int R, int Ns, int LINES, bool LF, int LS>
+__device__ __forceinline__ void pass_sm_any(float2* sm, const float2* __restrict__ tw) {
+  if constexpr (PREC != 0 && R == 16) {
+    auto ld = [&](int line, int i) { return sm[line * LS + pad(i)]; };
+    auto st = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
+    stockham_pass_tc<S, ADJ, L, Ns, LINES, LF, true>(tw, ld, st);
+  } else {
+    stockham_pass_sm<S, ADJ, L, R, Ns, LINES, LF, LS>(sm, tw);
+  }
+}
+
+// Passes [P, PEND) of the forward chain (sign S) in place in shared memory; LS is the
+// caller's line stride in float2 units.
+template <int S, int L, bool CONV, int LINES, bool LF, int LS, int P, int PEND, int PREC = 0>
+__device__ __forceinline__ void fwd_passes_smem(float2* sm, const float2* __restrict__ tw) {
+  if constexpr (P < PEND) {
+    constexpr int R = radix_at(L, CONV, P);
+    constexpr int Ns = ns_at(L, CONV, P);
+    pass_sm_any<PREC, S, false, L, R, Ns, LINES, LF, LS>(sm, tw);
+    __syncthreads();
+    fwd_passes_smem<S, L, CONV, LINES, LF, LS, P + 1, PEND, PREC>(sm, tw);
+  }
+}
+
+// Adjoint passes P-1 down to PEND (inclusive) in place in shared memory.
+template <int S, int L, bool CONV, int LINES, bool LF, int LS, int P, int PEND, int PREC = 0>
+__device__ __forceinline__ void adj_passes_smem(float2* sm, const float2* __restrict__ tw) {
+  if constexpr (P > PEND) {
+    constexpr int R = radix_at(L, CONV, P - 1);
+    constexpr int Ns = ns_at(L, CONV, P - 1);
+    pass_sm_any<PREC, S, true, L, R, Ns, LINES, LF, LS>(sm, tw);
+    __syncthreads();
+    adj_passes_smem<S, L, CONV, LINES, LF, LS, P - 1, PEND, PREC>(sm, tw);
+  }
+}
+
+}  // namespace gbd

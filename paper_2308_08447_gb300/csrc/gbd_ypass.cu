@@ -5,7 +5,7 @@
 
 namespace gbd {
 
-template <int L, int C_, bool INV>
+template <int L, int C_, bool INV, int PREC>
 __global__ void __launch_bounds__(C_ * L / GBD_E, min_blocks(C_ * L / GBD_E))
     y_pass_kernel(ColArgs a, const float2* __restrict__ tw) {
   constexpr int LINES = C_;
@@ -25,12 +25,12 @@ __global__ void __launch_bounds__(C_ * L / GBD_E, min_blocks(C_ * L / GBD_E))
       if (l0 + line < nl) a.dst[(l0 + line) * L + i] = v;
     };
     if constexpr (NP == 1) {
-      stockham_pass<-1, false, L, radix_at(L, false, 0), 1, LINES, false, false>(tw, gld, gst);
+      pass_any<PREC, -1, false, L, radix_at(L, false, 0), 1, LINES, false, false>(tw, gld, gst);
     } else {
-      stockham_pass<-1, false, L, radix_at(L, false, 0), 1, LINES, false, false>(tw, gld, sst);
+      pass_any<PREC, -1, false, L, radix_at(L, false, 0), 1, LINES, false, false>(tw, gld, sst);
       __syncthreads();
-      fwd_passes_smem<-1, L, false, LINES, false, LS, 1, NP - 1>(sm, tw);
-      stockham_pass<-1, false, L, radix_at(L, false, NP - 1), ns_at(L, false, NP - 1), LINES, false, false>(tw, sld,
+      fwd_passes_smem<-1, L, false, LINES, false, LS, 1, NP - 1, PREC>(sm, tw);
+      pass_any<PREC, -1, false, L, radix_at(L, false, NP - 1), ns_at(L, false, NP - 1), LINES, false, false>(tw, sld,
                                                                                                            gst);
     }
   } else {
@@ -41,13 +41,13 @@ __global__ void __launch_bounds__(C_ * L / GBD_E, min_blocks(C_ * L / GBD_E))
       if (y < ny && l0 + line < nl) a.dst[(l0 + line) * ny + y] = v;
     };
     if constexpr (NP == 1) {
-      stockham_pass<1, true, L, radix_at(L, false, 0), 1, LINES, false, false>(tw, gld, gst);
+      pass_any<PREC, 1, true, L, radix_at(L, false, 0), 1, LINES, false, false>(tw, gld, gst);
     } else {
-      stockham_pass<1, true, L, radix_at(L, false, NP - 1), ns_at(L, false, NP - 1), LINES, false, false>(tw, gld,
+      pass_any<PREC, 1, true, L, radix_at(L, false, NP - 1), ns_at(L, false, NP - 1), LINES, false, false>(tw, gld,
                                                                                                          sst);
       __syncthreads();
-      adj_passes_smem<1, L, false, LINES, false, LS, NP - 1, 1>(sm, tw);
-      stockham_pass<1, true, L, radix_at(L, false, 0), 1, LINES, false, false>(tw, sld, gst);
+      adj_passes_smem<1, L, false, LINES, false, LS, NP - 1, 1, PREC>(sm, tw);
+      pass_any<PREC, 1, true, L, radix_at(L, false, 0), 1, LINES, false, false>(tw, sld, gst);
     }
   }
 }
@@ -58,24 +58,31 @@ __global__ void __launch_bounds__(C_ * L / GBD_E, min_blocks(C_ * L / GBD_E))
 // ---- launchers -------------------------------------------------------------------------------
 
 // a == nullptr only prepares the kernel (shared-memory attribute), without a launch.
-template <int L, int C, bool INV>
+template <int L, int C, bool INV, int PREC>
 static void ypass_launch_t(const ColArgs* a, const float2* tw, cudaStream_t st) {
   constexpr int T = C * L / GBD_E;
   const size_t smem = (size_t)C * line_stride<L, false>() * sizeof(float2);
-  prep(y_pass_kernel<L, C, INV>, smem);
-  if (a) y_pass_kernel<L, C, INV><<<(unsigned)((a->lines_total + C - 1) / C), T, smem, st>>>(*a, tw);
+  prep(y_pass_kernel<L, C, INV, PREC>, smem);
+  if (a) y_pass_kernel<L, C, INV, PREC><<<(unsigned)((a->lines_total + C - 1) / C), T, smem, st>>>(*a, tw);
+}
+
+// prec < 0 (with a == nullptr) prepares both precisions
+template <int L, int C, bool INV>
+static void ypass_launch_p(int prec, const ColArgs* a, const float2* tw, cudaStream_t st) {
+  if (prec <= 0) ypass_launch_t<L, C, INV, 0>(a, tw, st);
+  if (prec != 0) ypass_launch_t<L, C, INV, 1>(a, tw, st);
 }
 
 #define GBD_Y_CASE(L)                                             \
   case L:                                                         \
     if (var <= 0)                                                 \
-      ypass_launch_t<L, ypass_lines(L, 0), INV>(a, tw, st);       \
+      ypass_launch_p<L, ypass_lines(L, 0), INV>(prec, a, tw, st);       \
     if (var != 0)                                                 \
-      ypass_launch_t<L, ypass_lines(L, 1), INV>(a, tw, st);       \
+      ypass_launch_p<L, ypass_lines(L, 1), INV>(prec, a, tw, st);       \
     return true;
 
 template <bool INV>
-static bool ypass_dispatch(int Py, int var, const ColArgs* a, const float2* tw, cudaStream_t st) {
+static bool ypass_dispatch(int Py, int var, int prec, const ColArgs* a, const float2* tw, cudaStream_t st) {
   switch (Py) {
     GBD_Y_CASE(4)
     GBD_Y_CASE(8)
@@ -92,15 +99,15 @@ static bool ypass_dispatch(int Py, int var, const ColArgs* a, const float2* tw, 
   }
 }
 
-bool launch_y_fwd(int var, const ColArgs& a, const float2* tw, cudaStream_t st) {
-  return ypass_dispatch<false>(a.Py, var, &a, tw, st);
+bool launch_y_fwd(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st) {
+  return ypass_dispatch<false>(a.Py, var, prec, &a, tw, st);
 }
-bool launch_y_inv(int var, const ColArgs& a, const float2* tw, cudaStream_t st) {
-  return ypass_dispatch<true>(a.Py, var, &a, tw, st);
+bool launch_y_inv(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st) {
+  return ypass_dispatch<true>(a.Py, var, prec, &a, tw, st);
 }
-bool prepare_y_passes(int Py) {
-  return ypass_dispatch<false>(Py, -1, nullptr, nullptr, nullptr) &&
-         ypass_dispatch<true>(Py, -1, nullptr, nullptr, nullptr);
+bool prepare_y_passes(int Py, int prec) {
+  return ypass_dispatch<false>(Py, -1, prec, nullptr, nullptr, nullptr) &&
+         ypass_dispatch<true>(Py, -1, prec, nullptr, nullptr, nullptr);
 }
 
 }  // namespace gbd
