@@ -156,6 +156,7 @@ def run_ours(args):
     import torch
 
     from paper_2308_08447_gb300 import gbdemag
+    from paper_2308_08447_gb300 import replicas
     from paper_2308_08447_gb300 import workloads as W
 
     rank, world, local = _dist_env()
@@ -176,9 +177,7 @@ def run_ours(args):
     cells = spec.cells
     evals_per_step = 4 * nsteps
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
+    barrier = replicas.barrier
 
     # warm-up
     for _ in range(args.warmup):
@@ -203,12 +202,9 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    t_total = sum(times) / 1e3
-    if dist is not None:
-        t = torch.tensor([t_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
-    value = world * cells * evals_per_step * args.steps / t_total / 1e9
+    # whole job: the cells x evaluations of every replica over the slowest replica's time
+    thr, t_total, _ = replicas.job_throughput(cells * evals_per_step * args.steps, sum(times) / 1e3, "cuda")
+    value = thr / 1e9
     ms_per_step = t_total * 1e3 / args.steps
 
     # end to end through the public API with host buffers
@@ -226,12 +222,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         if i > 0:
             e2e_times.append(time.perf_counter() - t0)
-    e2e_t = sum(e2e_times)
-    if dist is not None:
-        t = torch.tensor([e2e_t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e_value = world * cells * evals_per_step * len(e2e_times) / e2e_t / 1e9
+    e2e_thr, _, _ = replicas.job_throughput(cells * evals_per_step * len(e2e_times), sum(e2e_times), "cuda")
+    e2e_value = e2e_thr / 1e9
     assert np.isfinite(host_out.numpy()).all()
 
     # per-pass device time (CUDA events around every launch), one instrumented step
@@ -273,7 +265,7 @@ def run_ours(args):
             "roofline": roofline,
         }
         if world == 1 and not args.no_cpu_baseline:
-            result["cpu_baseline"] = cpu_baseline(spec, m0)
+            result["cpu_baseline"] = cpu_baseline(spec, m0, repeats=4)
     mesh.close()
     if dist is not None:
         dist.barrier()
@@ -281,15 +273,21 @@ def run_ours(args):
     return result
 
 
-def cpu_baseline(spec, m0, repeats=1):
+def oracle_tensor(spec):
+    """The oracle's tensor at every offset of the mesh (set-up of the CPU baseline, untimed)."""
+    from oracle import tensor as T
+    return T.tensor_all_offsets(spec.n, spec.cell)
+
+
+def cpu_baseline(spec, m0, repeats=1, Nf=None):
     """The FP64 oracle, as it stands, on the host cores: `repeats` RK4 steps of the full film
     (4 FFT-convolution demag evaluations each). Tensor set-up is outside the timed region."""
     import numpy as np
 
     from oracle import llg as L
-    from oracle import tensor as T
 
-    Nf = T.tensor_all_offsets(spec.n, spec.cell)
+    if Nf is None:
+        Nf = oracle_tensor(spec)
     m = m0.astype(np.float64)
     f = lambda v: L.rhs(v, Nf, spec.cell, spec.Ms, spec.A_ex, spec.alpha)
     t0 = time.perf_counter()
@@ -506,12 +504,11 @@ def run_reference(args):
     from paper_2308_08447_gb300 import workloads as W
     spec = W.thin_film()
     m0 = W.vortex_noise(spec.n, spec.cell, spec.seed)
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state; set-up (tensor) is excluded from timing
+    Nf = oracle_tensor(spec)   # set-up, untimed; the oracle has no warm-up state
     vals = []
     cb = None
     for _ in range(args.steps):
-        cb = cpu_baseline(spec, m0)
+        cb = cpu_baseline(spec, m0, Nf=Nf)
         vals.append(cb["value"])
     value = statistics.mean(vals)
     cb["value"] = value
