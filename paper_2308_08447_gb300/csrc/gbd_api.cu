@@ -42,7 +42,7 @@ struct gbd_mesh {
   float* acc = nullptr;     // RK4 state: k-sum and two stage buffers, each [3][N]
   float* bufA = nullptr;
   float* bufB = nullptr;
-  float2* tw = nullptr;     // twiddle table, GBD_TW_LEN entries
+  float2* tw = nullptr;     // twiddle levels, 2 GBD_TW_LEN entries
   bool kernel_set = false;
   // optional per-launch timing: events[2i], events[2i+1] bracket launch i of class cls[i]
   bool timing = false;
@@ -114,7 +114,7 @@ bool make_plan(int nx, int ny, int nz, Plan& p, const char** why) {
   p.bytes_T = (!p.film && ny > 1) ? (size_t)3 * nz * p.Hx * p.Py * sizeof(float2) : 0;
   p.bytes_K = p.film ? (size_t)p.Hx * p.Ky * sizeof(float4) : (size_t)p.Hx * p.Ky * p.Kz * 6 * sizeof(float);
   p.bytes_state = (size_t)3 * 3 * p.N * sizeof(float);
-  p.bytes_tw = (size_t)GBD_TW_LEN * sizeof(float2);
+  p.bytes_tw = (size_t)2 * GBD_TW_LEN * sizeof(float2);
   return true;
 }
 
@@ -323,12 +323,14 @@ gbd_status gbd_mesh_create(const gbd_mesh_desc* desc, gbd_mesh** out) {
                   std::string("cudaMalloc: ") + cudaGetErrorString(e));
     }
   }
-  // twiddles exp(-2 pi i m / GBD_TW_LEN), FP64 on the host, rounded to FP32
-  std::vector<float2> tw(GBD_TW_LEN);
-  for (int k = 0; k < GBD_TW_LEN; ++k) {
-    const double ang = -2.0 * 3.14159265358979323846264338327950288 * (double)k / GBD_TW_LEN;
-    tw[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-  }
+  // twiddle levels: exp(-2 pi i m / N) at index N + m for N = 1, 2, 4, ..., GBD_TW_LEN and
+  // m < N, FP64 on the host, rounded to FP32 (index 0 is unused)
+  std::vector<float2> tw(2 * GBD_TW_LEN, make_float2(1.f, 0.f));
+  for (int N = 1; N <= GBD_TW_LEN; N *= 2)
+    for (int k = 0; k < N; ++k) {
+      const double ang = -2.0 * 3.14159265358979323846264338327950288 * (double)k / N;
+      tw[N + k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
   e = cudaMemcpy(m->tw, tw.data(), p.bytes_tw, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     free_mesh_buffers(m);

@@ -11,37 +11,40 @@ namespace gbd {
 // k' = k for k <= P/2 and P - k above; components odd along that axis change sign there
 // (xy, yz odd in y; xz, yz odd in z). The 1/(Px Py Pz) and the minus sign of Eq. 1 are in K~.
 // The last forward pass, the product and the first adjoint pass run in registers on one
-// thread per butterfly position j, for all three components.
+// thread per butterfly position j, for the NC components that the product couples (lines
+// line0 + c * lstride, c < NC): all three in 3D; for a film, where N_xz = N_yz = 0, the
+// pair (x, y) and then z alone, which keeps fewer values live. mul(k, h0, h1, h2) gets the
+// NC values as (v0, v1, v2) with the missing ones aliased to the last present one.
 // ---------------------------------------------------------------------------------------------
 
-template <int L, int RL, int NSL, class LD, class ST, class MUL>
+template <int L, int RL, int NSL, class LD, class ST, class MUL, int NC = 3>
 __device__ __forceinline__ void fused_item(int line0, int lstride, int j, const float2* __restrict__ tw, LD ld, ST st,
                                            MUL mul) {
   constexpr int LR = L / RL;
-  float2 v[3][RL];
+  float2 v[NC][RL];
 #pragma unroll
-  for (int c = 0; c < 3; ++c)
+  for (int c = 0; c < NC; ++c)
 #pragma unroll
     for (int r = 0; r < RL; ++r) v[c][r] = ld(line0 + c * lstride, j + r * LR);
   if constexpr (RL > 1) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) butterfly<-1, RL, NSL, false>(v[c], j, tw);
+    for (int c = 0; c < NC; ++c) butterfly<-1, RL, NSL, false>(v[c], j, tw);
 #pragma unroll
-    for (int q = 0; q < RL; ++q) mul(j + q * LR, v[0][q], v[1][q], v[2][q]);
+    for (int q = 0; q < RL; ++q) mul(j + q * LR, v[0][q], v[NC > 1 ? 1 : 0][q], v[NC - 1][q]);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) butterfly<1, RL, NSL, true>(v[c], j, tw);
+    for (int c = 0; c < NC; ++c) butterfly<1, RL, NSL, true>(v[c], j, tw);
   } else {
-    mul(j, v[0][0], v[1][0], v[2][0]);
+    mul(j, v[0][0], v[NC > 1 ? 1 : 0][0], v[NC - 1][0]);
   }
 #pragma unroll
-  for (int c = 0; c < 3; ++c)
+  for (int c = 0; c < NC; ++c)
 #pragma unroll
     for (int r = 0; r < RL; ++r) st(line0 + c * lstride, j + r * LR, v[c][r]);
 }
 
 // film: one block = C columns kx, three components each, lines = c * C + cc.
 template <int L, int C_, int PREC>
-__global__ void __launch_bounds__(3 * C_ * L / GBD_E, min_blocks(3 * C_ * L / GBD_E))
+__global__ void __launch_bounds__(3 * C_ * L / GBD_E, min_blocks_film(3 * C_ * L / GBD_E))
     film_conv_kernel(ColArgs a, const float2* __restrict__ tw) {
   constexpr int C = C_;
   constexpr int LINES = 3 * C;
@@ -71,23 +74,33 @@ __global__ void __launch_bounds__(3 * C_ * L / GBD_E, min_blocks(3 * C_ * L / GB
     for (int it = threadIdx.x; it < C * LR; it += T) {
       const int cc = it / LR, j = it % LR;
       const int kx = kx0 + cc;
-      auto mul = [&](int ky, float2& m0, float2& m1, float2& m2) {
-        if (kx >= Hx) return;
+      auto kfetch = [&](int ky, float& sy) {
         int kyp = ky;
-        float sy = 1.f;
+        sy = 1.f;
         if (L > 1 && ky > L / 2) {
           kyp = L - ky;
           sy = -1.f;
         }
-        const float4 k4 = __ldg(a.Kf + (long long)kx * KY + kyp);
+        return __ldg(a.Kf + (long long)kx * KY + kyp);
+      };
+      auto mulxy = [&](int ky, float2& m0, float2& m1, float2&) {
+        if (kx >= Hx) return;
+        float sy;
+        const float4 k4 = kfetch(ky, sy);
         const float kxy = sy * k4.w;
         const float2 h0 = make_float2(k4.x * m0.x + kxy * m1.x, k4.x * m0.y + kxy * m1.y);
         const float2 h1 = make_float2(kxy * m0.x + k4.y * m1.x, kxy * m0.y + k4.y * m1.y);
-        m2 = make_float2(k4.z * m2.x, k4.z * m2.y);
         m0 = h0;
         m1 = h1;
       };
-      fused_item<L, RL, NSL>(cc, C, j, tw, ld, st, mul);
+      auto mulz = [&](int ky, float2&, float2&, float2& m2) {
+        if (kx >= Hx) return;
+        float sy;
+        const float4 k4 = kfetch(ky, sy);
+        m2 = make_float2(k4.z * m2.x, k4.z * m2.y);
+      };
+      fused_item<L, RL, NSL, decltype(ld), decltype(st), decltype(mulxy), 2>(cc, C, j, tw, ld, st, mulxy);
+      fused_item<L, RL, NSL, decltype(ld), decltype(st), decltype(mulz), 1>(cc + 2 * C, C, j, tw, ld, st, mulz);
     }
   };
 

@@ -22,9 +22,11 @@
 // Shared memory rows are padded: element i of a line sits at i + i/16, which makes the
 // stride-16 accesses of the Ns = 1 pass and its adjoint conflict free.
 //
-// Twiddles come from one table tw[m] = exp(-2 pi i m / GBD_TW_LEN) written on the host
-// in FP64 and rounded to FP32. A butterfly loads w, w^2, w^4, w^8 and forms the other
-// powers with at most three complex products.
+// Twiddles come from one table of all power-of-two levels, written on the host in FP64 and
+// rounded to FP32: level N (1 <= N <= GBD_TW_LEN) holds E_N[m] = exp(-2 pi i m / N),
+// m in [0, N), at index N + m. A butterfly of a pass (Ns, R) at position k loads
+// w^r = E_(Ns R / r)[k] for r = 1, 2, 4, 8, so the lanes of a warp, which hold consecutive
+// k, read consecutive entries; it forms the other powers with at most three complex products.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -45,11 +47,16 @@ __device__ __forceinline__ float2 cmul_i(float2 a) {  // a * (S i)
   return S > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
-// exp(S 2 pi i m / GBD_TW_LEN)
+// exp(S 2 pi i m / N) for a power of two N <= GBD_TW_LEN and 0 <= m < N
+template <int S>
+__device__ __forceinline__ float2 twiddle_at(const float2* __restrict__ tw, int N, int m) {
+  float2 w = __ldg(tw + N + m);
+  return S < 0 ? w : cconj(w);
+}
+// exp(S 2 pi i m / GBD_TW_LEN) for any m
 template <int S>
 __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int m) {
-  float2 w = __ldg(tw + (m & (GBD_TW_LEN - 1)));
-  return S < 0 ? w : cconj(w);
+  return twiddle_at<S>(tw, GBD_TW_LEN, m & (GBD_TW_LEN - 1));
 }
 
 // ---- radix decomposition (compile time) -------------------------------------------------
@@ -160,24 +167,23 @@ __device__ __forceinline__ void dft(float2* x) {
 // powers and one product are live next to the data.
 template <int S, int R, int Ns>
 __device__ __forceinline__ void apply_twiddles(float2* v, int k, const float2* __restrict__ tw) {
-  constexpr int step = GBD_TW_LEN / (Ns * R);
-  const int m = k * step;
-  const float2 w1 = twiddle<S>(tw, m);
+  constexpr int NR = Ns * R;   // w = E_NR, and w^r = E_(NR / r) at the same k < Ns
+  const float2 w1 = twiddle_at<S>(tw, NR, k);
   v[1] = cmul(v[1], w1);
   if constexpr (R >= 4) {
-    const float2 w2 = twiddle<S>(tw, 2 * m);
+    const float2 w2 = twiddle_at<S>(tw, NR / 2, k);
     const float2 w3 = cmul(w1, w2);
     v[2] = cmul(v[2], w2);
     v[3] = cmul(v[3], w3);
     if constexpr (R >= 8) {
-      const float2 w4 = twiddle<S>(tw, 4 * m);
+      const float2 w4 = twiddle_at<S>(tw, NR / 4, k);
       const float2 w5 = cmul(w1, w4), w6 = cmul(w2, w4), w7 = cmul(w3, w4);
       v[4] = cmul(v[4], w4);
       v[5] = cmul(v[5], w5);
       v[6] = cmul(v[6], w6);
       v[7] = cmul(v[7], w7);
       if constexpr (R >= 16) {
-        const float2 w8 = twiddle<S>(tw, 8 * m);
+        const float2 w8 = twiddle_at<S>(tw, NR / 8, k);
         v[8] = cmul(v[8], w8);
         v[9] = cmul(v[9], cmul(w1, w8));
         v[10] = cmul(v[10], cmul(w2, w8));

@@ -37,7 +37,6 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
   constexpr int NP = npasses(LX, false);
   constexpr int HX = LX + 1;
   constexpr int HALF = LX / 2;
-  constexpr int TWS = GBD_TW_LEN / (2 * LX);   // W_Px^k = tw[k * TWS]
   constexpr int FL = NP >= 1 ? LX : 2 * LX;    // real samples the forward transform reads
   extern __shared__ float2 sm[];
   const int r0 = blockIdx.x * RB;
@@ -111,7 +110,7 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
       const int t2 = e / RG;
       const int c = t2 % 3;
       const int k = t2 / 3;
-      const float2 wp = twiddle<-1>(tw, k * TWS);  // W^k
+      const float2 wp = twiddle_at<-1>(tw, 2 * LX, k);  // W^k, W = exp(-2 pi i / Px)
       const float2 wm = cconj(wp);                  // W^-k
 #pragma unroll
       for (int u = 0; u < VR; ++u) {
@@ -386,7 +385,7 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
     const int t2 = e / RG;
     const int c = t2 % 3;
     const int k = t2 / 3;
-    const float2 wp = twiddle<-1>(tw, k * TWS);  // W^k
+    const float2 wp = twiddle_at<-1>(tw, 2 * LX, k);  // W^k, W = exp(-2 pi i / Px)
     const float2 wm = cconj(wp);
     float2 xk[VR], xl[VR];
 #pragma unroll

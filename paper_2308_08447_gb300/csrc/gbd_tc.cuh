@@ -93,7 +93,7 @@ template <int S, bool ADJ, int L, int Ns, int LINES, bool LF, bool SYNC_MID, cla
 __device__ __forceinline__ void stockham_pass_tc(const float2* __restrict__ tw, LD ld, ST st) {
   constexpr int R = 16;
   constexpr int LR = L / R;
-  constexpr int step = GBD_TW_LEN / (Ns * R);
+  constexpr int NR = Ns * R;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
@@ -118,7 +118,7 @@ __device__ __forceinline__ void stockham_pass_tc(const float2* __restrict__ tw, 
     for (int i = 0; i < 4; ++i) {
       const int r = rin[i];
       float2 v = ld(line, ADJ ? (j - k) * R + k + r * Ns : j + r * LR);
-      if (!ADJ && Ns > 1 && r > 0) v = cmul(v, twiddle<S>(tw, r * k * step));
+      if (!ADJ && Ns > 1 && r > 0) v = cmul(v, twiddle_at<S>(tw, NR, (r * k) & (NR - 1)));
       x[grp][i] = v;
     }
   }
@@ -155,7 +155,7 @@ __device__ __forceinline__ void stockham_pass_tc(const float2* __restrict__ tw, 
       for (int h = 0; h < 2; ++h) {
         const int q = g + 8 * h;
         float2 v = make_float2(y[0][2 * h + c], y[1][2 * h + c]);
-        if (ADJ && Ns > 1 && q > 0) v = cmul(v, twiddle<S>(tw, q * k * step));
+        if (ADJ && Ns > 1 && q > 0) v = cmul(v, twiddle_at<S>(tw, NR, (q * k) & (NR - 1)));
         st(line, ADJ ? j + q * LR : (j - k) * R + k + q * Ns, v);
       }
     }

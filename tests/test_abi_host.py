@@ -65,7 +65,8 @@ def test_mesh_bytes_counts_buffers(g):
     S = 3 * 1025 * 1024 * 8
     K = 1025 * 1025 * 16
     state = 9 * N * 4
-    assert b == S + K + state + 8192 * 8
+    twiddles = 2 * 8192 * 8   # all power-of-two levels up to 8192 entries
+    assert b == S + K + state + twiddles
 
 
 def _scale(X, Y, Z, cell):
