@@ -497,6 +497,74 @@ def run_3d(args):
     return res
 
 
+def run_cufft(args):
+    """Film 1024 x 1024 x 1: one demag evaluation by this library (gbd_demag) beside the same
+    zero-padded convolution written with torch.fft (cuFFT R2C / C2R and torch elementwise ops
+    for the kernel product), both timed back to back with CUDA events on one stream. cuFFT is a
+    comparison only; it is never on the library's path."""
+    import numpy as np
+    import torch
+
+    from paper_2308_08447_gb300 import gbdemag
+    from paper_2308_08447_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    gbdemag.load()
+    spec = W.thin_film()
+    nx, ny, nz = spec.n
+    mesh = gbdemag.Mesh(spec.n, spec.cell, spec.Ms, A_ex=spec.A_ex, alpha=spec.alpha)
+    mesh.autotune()
+    M = torch.from_numpy(spec.Ms * W.vortex_noise(spec.n, spec.cell, spec.seed)).cuda()
+    H = torch.empty_like(M)
+    stream = torch.cuda.current_stream()
+    reps = 200
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / reps
+
+    t_ours = timed(lambda: mesh.demag(M, H))
+    H_ours = H.clone()
+    # full (Py, Hx) kernel from the library's FP64 packed spectrum; rows ky > Py/2 mirror, with
+    # the sign flip of N_xy (odd in y). The stored spectrum carries -1/(Px Py); torch's inverse
+    # divides by Px Py itself, so the product uses Px Py times the stored values.
+    Px, Py, Pz, Hx, Ky, Kz = gbdemag.gbd_plan_dims(mesh.desc)
+    ks = gbdemag.gbd_kernel_spectrum_host(mesh.desc)[:4, 0] * (Px * Py)     # (4, Ky, Hx)
+    rows = np.concatenate([np.arange(Ky), Py - np.arange(Ky, Py)])
+    sign = np.where(np.arange(Py) < Ky, 1.0, -1.0)[:, None]
+    kf = ks[:, rows, :]
+    kf[3] *= sign
+    Kt = torch.from_numpy(kf.astype(np.float32)).cuda()
+    Mp = M[:, 0]
+
+    def cufft_demag():
+        X = torch.fft.rfft2(Mp, s=(Py, Px))
+        Y = torch.stack([Kt[0] * X[0] + Kt[3] * X[1], Kt[3] * X[0] + Kt[1] * X[1], Kt[2] * X[2]])
+        return torch.fft.irfft2(Y, s=(Py, Px))[:, :ny, :nx]
+
+    t_cufft = timed(cufft_demag)
+    H_cufft = cufft_demag().unsqueeze(1)
+    d = (H_cufft - H_ours).double()
+    e = float(d.pow(2).sum(0).sqrt().max() / H_ours.double().pow(2).sum(0).sqrt().max())
+    mesh.close()
+    return {"metric": METRIC, "value": round(spec.cells / t_ours / 1e3, 3), "unit": UNIT, "n_gpus": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "steps": reps, "warmup": max(args.warmup, 3),
+            "config": {"workload": "thin film 1024x1024x1 demag evaluation: this library vs torch.fft (cuFFT)",
+                       "l2": "not flushed (back-to-back evaluations, as inside a time loop)"},
+            "ours_demag_us": round(t_ours, 2), "cufft_demag_us": round(t_cufft, 2),
+            "cufft_gcell_demag_per_s": round(spec.cells / t_cufft / 1e3, 3),
+            "speedup_vs_cufft": round(t_cufft / t_ours, 3), "e_inf_ours_vs_cufft": e}
+
+
 def run_reference(args):
     rank, world, local = _dist_env()
     if rank != 0:
@@ -529,7 +597,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--llg-steps", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="film", choices=["film", "batch", "serve", "3d"])
+    ap.add_argument("--workload", default="film", choices=["film", "batch", "serve", "3d", "cufft"])
     ap.add_argument("--oracle-3d", action="store_true", help="3d: FP64 oracle of the full mesh (minutes, ~30 GB)")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--requests", type=int, default=48)
@@ -545,6 +613,8 @@ def main():
         res = run_serve(args)
     elif args.workload == "3d":
         res = run_3d(args)
+    elif args.workload == "cufft":
+        res = run_cufft(args)
     else:
         res = run_ours(args)
     if res is not None:

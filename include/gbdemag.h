@@ -89,6 +89,20 @@ gbd_status gbd_mesh_bytes(const gbd_mesh_desc* desc, size_t* out);
  * GBD_KERNEL_CACHE_BYTES (environment variable, default 4 GiB). */
 gbd_status gbd_set_kernel(gbd_mesh* mesh, void* stream);
 
+/* Like gbd_set_kernel, but with the caller's FP64 tensor instead of the built-in one (Eq. 1
+ * holds for any interaction tensor with the demag tensor's symmetries, e.g. one summed over
+ * periodic images or a dipole-dipole kernel). N6: host array [6][2nz-1][2ny-1][2nx-1] of
+ * (xx, yy, zz, xy, xz, yz), element (X, Y, Z) at index ((c (2nz-1) + Z+nz-1) (2ny-1) + Y+ny-1)
+ * (2nx-1) + X+nx-1, for offsets |X| < nx, |Y| < ny, |Z| < nz; read only during the call.
+ * Each component must be finite and have the parities of the demag tensor (xx, yy, zz even in
+ * X, Y, Z; xy odd in X and Y; xz odd in X and Z; yz odd in Y and Z), to within
+ * GBD_TENSOR_SYM_TOL times the largest magnitude in N6; otherwise GBD_EINVAL and nothing
+ * changes.
+ * Only the octant X, Y, Z >= 0 is then used. The result is not put into the host cache.
+ * Blocks until the copy is done. */
+#define GBD_TENSOR_SYM_TOL 1e-9
+gbd_status gbd_set_kernel_tensor(gbd_mesh* mesh, const double* N6, void* stream);
+
 /* H = H_d(M) of Eq. 1. M, H: device [3][nz][ny][nx] float32, A/m; M and H must not overlap. */
 gbd_status gbd_demag(gbd_mesh* mesh, const float* M, float* H, void* stream);
 
@@ -203,6 +217,11 @@ gbd_status gbd_plan_dims(const gbd_mesh_desc* desc, int out[6]);
 /* The FP64 packed kernel spectrum that gbd_set_kernel uploads (before rounding to FP32),
  * layout [6][Kz][Ky][Hx]; count must equal 6*Kz*Ky*Hx. Components xz, yz are zero when nz = 1. */
 gbd_status gbd_kernel_spectrum_host(const gbd_mesh_desc* desc, double* out, size_t count);
+
+/* The FP64 packed spectrum that gbd_set_kernel_tensor would upload for the caller tensor N6
+ * (layout and checks as there), layout [6][Kz][Ky][Hx]; count must equal 6*Kz*Ky*Hx. */
+gbd_status gbd_kernel_spectrum_from_tensor_host(const gbd_mesh_desc* desc, const double* N6, double* out,
+                                                size_t count);
 
 #ifdef __cplusplus
 }

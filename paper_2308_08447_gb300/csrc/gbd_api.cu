@@ -290,6 +290,22 @@ gbd_status gbd_kernel_spectrum_host(const gbd_mesh_desc* desc, double* out, size
   return GBD_OK;
 }
 
+static gbd_status spectrum_of_tensor(const gbd::Plan& p, const double* N6, std::vector<double>& spec);
+
+gbd_status gbd_kernel_spectrum_from_tensor_host(const gbd_mesh_desc* desc, const double* N6, double* out,
+                                                size_t count) {
+  gbd::Plan p;
+  gbd_status s = check_desc(desc, p);
+  if (s != GBD_OK) return s;
+  const size_t need = (size_t)6 * p.Kz * p.Ky * p.Hx;
+  if (!out || count != need) return fail(GBD_EINVAL, "out is NULL or count != 6*Kz*Ky*Hx");
+  std::vector<double> spec;
+  s = spectrum_of_tensor(p, N6, spec);
+  if (s != GBD_OK) return s;
+  std::memcpy(out, spec.data(), need * sizeof(double));
+  return GBD_OK;
+}
+
 gbd_status gbd_mesh_create(const gbd_mesh_desc* desc, gbd_mesh** out) {
   if (!out) return fail(GBD_EINVAL, "out is NULL");
   *out = nullptr;
@@ -445,22 +461,10 @@ void spec_cache_put(const GeoKey& k, std::shared_ptr<const std::vector<float>> d
 }
 }  // namespace
 
-gbd_status gbd_set_kernel(gbd_mesh* m, void* stream) {
-  if (!m) return fail(GBD_EINVAL, "mesh is NULL");
-  gbd_status s = check_device(m);
-  if (s != GBD_OK) return s;
+// Packs the FP64 spectrum [6][Kz][Ky][Hx] into the device layout, uploads it on st and waits;
+// a geometry key puts the packed copy into the host cache.
+static gbd_status upload_spectrum(gbd_mesh* m, const std::vector<double>& spec, cudaStream_t st, const GeoKey* key) {
   const gbd::Plan& p = m->p;
-  const GeoKey key{p.nx, p.ny, p.nz, m->d.dx, m->d.dy, m->d.dz};
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (auto hit = spec_cache_get(key)) {
-    cudaError_t e = cudaMemcpyAsync(m->K, hit->data(), p.bytes_K, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "kernel upload");
-    m->kernel_set = true;
-    return GBD_OK;
-  }
-  std::vector<double> spec;
-  if (!gbdt::kernel_spectrum(p, m->d.dx, m->d.dy, m->d.dz, spec)) return fail(GBD_ENOMEM, "host allocation failed");
   const size_t plane = (size_t)p.Ky * p.Hx;
   const size_t comp = (size_t)p.Kz * plane;
   auto packed_ptr = std::make_shared<std::vector<float>>();
@@ -488,9 +492,51 @@ gbd_status gbd_set_kernel(gbd_mesh* m, void* stream) {
   cudaError_t e = cudaMemcpyAsync(m->K, packed.data(), p.bytes_K, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "kernel upload");
-  spec_cache_put(key, packed_ptr);
+  if (key) spec_cache_put(*key, packed_ptr);
   m->kernel_set = true;
   return GBD_OK;
+}
+
+gbd_status gbd_set_kernel(gbd_mesh* m, void* stream) {
+  if (!m) return fail(GBD_EINVAL, "mesh is NULL");
+  gbd_status s = check_device(m);
+  if (s != GBD_OK) return s;
+  const gbd::Plan& p = m->p;
+  const GeoKey key{p.nx, p.ny, p.nz, m->d.dx, m->d.dy, m->d.dz};
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (auto hit = spec_cache_get(key)) {
+    cudaError_t e = cudaMemcpyAsync(m->K, hit->data(), p.bytes_K, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel upload");
+    m->kernel_set = true;
+    return GBD_OK;
+  }
+  std::vector<double> spec;
+  if (!gbdt::kernel_spectrum(p, m->d.dx, m->d.dy, m->d.dz, spec)) return fail(GBD_ENOMEM, "host allocation failed");
+  return upload_spectrum(m, spec, st, &key);
+}
+
+// Spectrum of a caller tensor [6][2nz-1][2ny-1][2nx-1] (see gbd_set_kernel_tensor).
+static gbd_status spectrum_of_tensor(const gbd::Plan& p, const double* N6, std::vector<double>& spec) {
+  if (!N6) return fail(GBD_EINVAL, "tensor is NULL");
+  std::vector<double> oct;
+  const int r = gbdt::octant_from_full(p, N6, oct, GBD_TENSOR_SYM_TOL);
+  if (r < 0) return fail(GBD_ENOMEM, "host allocation failed");
+  if (r > 0)
+    return fail(GBD_EINVAL, "tensor has a non-finite value or lacks the demag parities (xx, yy, zz even; "
+                            "xy odd in X, Y; xz odd in X, Z; yz odd in Y, Z)");
+  if (!gbdt::spectrum_from_octant(p, oct, spec)) return fail(GBD_ENOMEM, "host allocation failed");
+  return GBD_OK;
+}
+
+gbd_status gbd_set_kernel_tensor(gbd_mesh* m, const double* N6, void* stream) {
+  if (!m) return fail(GBD_EINVAL, "mesh is NULL");
+  gbd_status s = check_device(m);
+  if (s != GBD_OK) return s;
+  std::vector<double> spec;
+  s = spectrum_of_tensor(m->p, N6, spec);
+  if (s != GBD_OK) return s;
+  return upload_spectrum(m, spec, static_cast<cudaStream_t>(stream), nullptr);
 }
 
 static gbd_status ready(gbd_mesh* m) {

@@ -44,4 +44,10 @@ void newell_closed_form(double X, double Y, double Z, double dx, double dy, doub
 void dipole_quadrature(double X, double Y, double Z, double dx, double dy, double dz, int G, double out[6]);
 void tensor_at(int X, int Y, int Z, double dx, double dy, double dz, double out[6]);
 bool kernel_spectrum(const gbd::Plan& p, double dx, double dy, double dz, std::vector<double>& out);
+// Packed spectrum from the octant X, Y, Z >= 0 of the six components, layout [6][nz][ny][nx].
+bool spectrum_from_octant(const gbd::Plan& p, const std::vector<double>& oct, std::vector<double>& out);
+// Octant of a caller tensor [6][2nz-1][2ny-1][2nx-1] after checking that the values are finite
+// and have the tensor's parities within tol times the largest magnitude of all components.
+// Returns 0, 1 (not finite or not symmetric) or -1 (allocation failure).
+int octant_from_full(const gbd::Plan& p, const double* full, std::vector<double>& oct, double tol);
 }  // namespace gbdt

@@ -25,6 +25,7 @@
 // Each G is computed with a complex FFT of the symmetric extension of the line.
 #include <cmath>
 #include <complex>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -223,7 +224,6 @@ bool kernel_spectrum(const gbd::Plan& p, double dx, double dy, double dz, std::v
   std::vector<double> oct;
   try {
     oct.resize((size_t)Noct * 6);
-    out.assign((size_t)6 * p.Kz * p.Ky * p.Hx, 0.0);
   } catch (...) {
     return false;
   }
@@ -233,6 +233,59 @@ bool kernel_spectrum(const gbd::Plan& p, double dx, double dy, double dz, std::v
     double v[6];
     tensor_at(X, Y, Z, dx, dy, dz, v);
     for (int c = 0; c < 6; ++c) oct[(size_t)c * Noct + i] = v[c];
+  }
+  return spectrum_from_octant(p, oct, out);
+}
+
+// Index of offset (X, Y, Z) in a caller tensor laid out [6][2nz-1][2ny-1][2nx-1].
+static inline size_t full_index(const gbd::Plan& p, int c, int X, int Y, int Z) {
+  const size_t wx = 2 * (size_t)p.nx - 1, wy = 2 * (size_t)p.ny - 1, wz = 2 * (size_t)p.nz - 1;
+  return (((size_t)c * wz + (size_t)(Z + p.nz - 1)) * wy + (size_t)(Y + p.ny - 1)) * wx + (size_t)(X + p.nx - 1);
+}
+
+int octant_from_full(const gbd::Plan& p, const double* full, std::vector<double>& oct, double tol) {
+  const int nx = p.nx, ny = p.ny, nz = p.nz;
+  const long long Noct = (long long)nx * ny * nz;
+  try {
+    oct.resize((size_t)Noct * 6);
+  } catch (...) {
+    return -1;
+  }
+  double mx = 0.0;
+  for (int c = 0; c < 6; ++c)
+    for (int Z = 1 - nz; Z < nz; ++Z)
+      for (int Y = 1 - ny; Y < ny; ++Y)
+        for (int X = 1 - nx; X < nx; ++X) mx = std::fmax(mx, std::fabs(full[full_index(p, c, X, Y, Z)]));
+  const double lim = tol * mx;
+  for (int c = 0; c < 6; ++c) {
+    for (int Z = 1 - nz; Z < nz; ++Z)
+      for (int Y = 1 - ny; Y < ny; ++Y)
+        for (int X = 1 - nx; X < nx; ++X) {
+          const double v = full[full_index(p, c, X, Y, Z)];
+          if (!std::isfinite(v)) return 1;
+          const double sgn = (X < 0 ? PARITY[c][0] : 1) * (Y < 0 ? PARITY[c][1] : 1) * (Z < 0 ? PARITY[c][2] : 1);
+          const double ref = sgn * full[full_index(p, c, std::abs(X), std::abs(Y), std::abs(Z))];
+          if (std::fabs(v - ref) > lim) return 1;
+          // an odd component is zero on its odd axis planes
+          if (((PARITY[c][0] < 0 && X == 0) || (PARITY[c][1] < 0 && Y == 0) || (PARITY[c][2] < 0 && Z == 0)) &&
+              std::fabs(v) > lim)
+            return 1;
+        }
+    for (int Z = 0; Z < nz; ++Z)
+      for (int Y = 0; Y < ny; ++Y)
+        for (int X = 0; X < nx; ++X)
+          oct[(size_t)c * Noct + ((size_t)Z * ny + Y) * nx + X] = full[full_index(p, c, X, Y, Z)];
+  }
+  return 0;
+}
+
+bool spectrum_from_octant(const gbd::Plan& p, const std::vector<double>& oct, std::vector<double>& out) {
+  const int nx = p.nx, ny = p.ny, nz = p.nz;
+  const long long Noct = (long long)nx * ny * nz;
+  try {
+    out.assign((size_t)6 * p.Kz * p.Ky * p.Hx, 0.0);
+  } catch (...) {
+    return false;
   }
   Fft1 fx(p.Px), fy(p.Py), fz(p.Pz);
   const double scale = 1.0 / ((double)p.Px * p.Py * p.Pz);

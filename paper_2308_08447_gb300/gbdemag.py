@@ -43,6 +43,7 @@ _SIG = {
     "gbd_mesh_create": [ctypes.POINTER(gbd_mesh_desc), ctypes.POINTER(_P)],
     "gbd_mesh_bytes": [ctypes.POINTER(gbd_mesh_desc), ctypes.POINTER(ctypes.c_size_t)],
     "gbd_set_kernel": [_P, _P],
+    "gbd_set_kernel_tensor": [_P, ctypes.POINTER(_D), _P],
     "gbd_demag": [_P, _P, _P, _P],
     "gbd_effective_field": [_P, _P, _P, _P],
     "gbd_llg_rhs": [_P, _P, _P, _P],
@@ -51,6 +52,8 @@ _SIG = {
     "gbd_tensor_at": [ctypes.POINTER(gbd_mesh_desc), _I, _I, _I, ctypes.POINTER(_D)],
     "gbd_plan_dims": [ctypes.POINTER(gbd_mesh_desc), ctypes.POINTER(_I)],
     "gbd_kernel_spectrum_host": [ctypes.POINTER(gbd_mesh_desc), ctypes.POINTER(_D), ctypes.c_size_t],
+    "gbd_kernel_spectrum_from_tensor_host": [ctypes.POINTER(gbd_mesh_desc), ctypes.POINTER(_D), ctypes.POINTER(_D),
+                                             ctypes.c_size_t],
     "gbd_demag_noalloc": [_P, _P, _P, _P],
     "gbd_mesh_autotune": [_P, _P],
     "gbd_mesh_get_tuning": [_P, ctypes.POINTER(_I)],
@@ -141,6 +144,22 @@ def gbd_mesh_bytes(desc):
 
 def gbd_set_kernel(mesh, stream=None):
     _check(load().gbd_set_kernel(mesh, _stream_ptr(stream)))
+
+
+def _tensor_arg(N6, n):
+    """C-contiguous float64 copy of a caller tensor of shape (6, 2nz-1, 2ny-1, 2nx-1)."""
+    import numpy as np
+    nx, ny, nz = n
+    want = (6, 2 * nz - 1, 2 * ny - 1, 2 * nx - 1)
+    arr = np.ascontiguousarray(N6, dtype=np.float64)
+    if arr.shape != want:
+        raise ValueError("tensor shape %s != %s" % (arr.shape, want))
+    return arr
+
+
+def gbd_set_kernel_tensor(mesh, N6, n, stream=None):
+    arr = _tensor_arg(N6, n)
+    _check(load().gbd_set_kernel_tensor(mesh, arr.ctypes.data_as(ctypes.POINTER(_D)), _stream_ptr(stream)))
 
 
 def gbd_demag(mesh, M, H, shape, stream=None):
@@ -243,6 +262,16 @@ def gbd_kernel_spectrum_host(desc):
     return out
 
 
+def gbd_kernel_spectrum_from_tensor_host(desc, N6):
+    import numpy as np
+    Px, Py, Pz, Hx, Ky, Kz = gbd_plan_dims(desc)
+    arr = _tensor_arg(N6, (desc.nx, desc.ny, desc.nz))
+    out = np.zeros((6, Kz, Ky, Hx), dtype=np.float64)
+    _check(load().gbd_kernel_spectrum_from_tensor_host(ctypes.byref(desc), arr.ctypes.data_as(ctypes.POINTER(_D)),
+                                                       out.ctypes.data_as(ctypes.POINTER(_D)), out.size))
+    return out
+
+
 # ---- convenience wrapper --------------------------------------------------------------------
 
 class Mesh:
@@ -256,6 +285,10 @@ class Mesh:
         self.handle = gbd_mesh_create(self.desc)
         if set_kernel:
             gbd_set_kernel(self.handle, stream)
+
+    def set_kernel_tensor(self, N6, stream=None):
+        """Replace the kernel by the caller's FP64 tensor, shape (6, 2nz-1, 2ny-1, 2nx-1)."""
+        gbd_set_kernel_tensor(self.handle, N6, self.n, stream)
 
     def demag(self, M, H, stream=None):
         gbd_demag(self.handle, M, H, self.shape, stream)

@@ -116,3 +116,78 @@ def test_library_spectrum_matches_oracle_fft(g, n, cell):
     if n[2] == 1:
         want[4:] = 0.0
     assert np.abs(spec - want).max() <= 1e-11 * np.abs(want).max()
+
+
+# ---- caller tensors (gbd_set_kernel_tensor / gbd_kernel_spectrum_from_tensor_host) ----------
+
+@pytest.mark.parametrize("n,cell", [((8, 6, 1), (2e-9, 2e-9, 3e-9)), ((5, 4, 3), (2e-9, 3e-9, 4e-9)),
+                                    ((1, 1, 1), (3e-9, 3e-9, 3e-9)), ((1, 7, 4), (1e-9, 1e-9, 2e-9))])
+def test_spectrum_of_caller_tensor_matches_numpy_fft(g, n, cell):
+    # the oracle's tensor through the caller path equals numpy's FFT of the placed tensor
+    desc = g.make_desc(n, cell, 8e5)
+    Px, Py, Pz, Hx, Ky, Kz = g.gbd_plan_dims(desc)
+    Nf = T.tensor_all_offsets(n, cell)
+    spec = g.gbd_kernel_spectrum_from_tensor_host(desc, Nf)
+    Kt = C.place_kernel(Nf, n, (Px, Py, Pz))
+    Kh = np.fft.fft(np.fft.fft(np.fft.rfft(Kt, axis=3), axis=2), axis=1)
+    want = -Kh.real[:, :Kz, :Ky, :] / (Px * Py * Pz)
+    if n[2] == 1:
+        want[4:] = 0.0
+    assert np.abs(spec - want).max() <= 1e-12 * np.abs(want).max()
+    # and agrees with the built-in tensor's spectrum to the tensors' agreement (<= 1e-8 scale)
+    assert np.abs(spec - g.gbd_kernel_spectrum_host(desc)).max() <= 1e-8 * np.abs(want).max()
+
+
+def _sparse_tensor(n, a, b, c, v, u):
+    """Self term diag(a, b, c); N_xy = v sign(X) sign(Y) at (+-1, +-1, 0); N_xz = u sign(X) sign(Z)
+    at (+-1, 0, +-1); everything else 0."""
+    nx, ny, nz = n
+    N6 = np.zeros((6, 2 * nz - 1, 2 * ny - 1, 2 * nx - 1))
+    o = (nz - 1, ny - 1, nx - 1)
+    N6[0][o], N6[1][o], N6[2][o] = a, b, c
+    for sx in (1, -1):
+        for sy in (1, -1):
+            N6[3][o[0], o[1] + sy, o[2] + sx] = v * sx * sy
+        for sz in (1, -1):
+            N6[4][o[0] + sz, o[1], o[2] + sx] = u * sx * sz
+    return N6
+
+
+def test_spectrum_of_sparse_tensor_closed_form(g):
+    # DFT of the sparse tensor by hand: a constant for the self term, and
+    # sum_(X,Y=+-1) v sgn(X) sgn(Y) e^{-i(aX+bY)} = -4 v sin(a) sin(b); stored: -F / (Px Py Pz)
+    n = (4, 3, 2)
+    a_, b_, c_, v, u = 0.3, 0.25, 0.45, 0.07, -0.05
+    desc = g.make_desc(n, (2e-9, 2e-9, 2e-9), 8e5)
+    Px, Py, Pz, Hx, Ky, Kz = g.gbd_plan_dims(desc)
+    spec = g.gbd_kernel_spectrum_from_tensor_host(desc, _sparse_tensor(n, a_, b_, c_, v, u))
+    P = Px * Py * Pz
+    kz, ky, kx = np.meshgrid(np.arange(Kz), np.arange(Ky), np.arange(Hx), indexing="ij")
+    sx, sy, sz = np.sin(2 * np.pi * kx / Px), np.sin(2 * np.pi * ky / Py), np.sin(2 * np.pi * kz / Pz)
+    want = np.stack([np.full(kx.shape, -a_ / P), np.full(kx.shape, -b_ / P), np.full(kx.shape, -c_ / P),
+                     4 * v * sx * sy / P, 4 * u * sx * sz / P, np.zeros(kx.shape)])
+    assert np.abs(spec - want).max() <= 1e-15
+
+
+def test_caller_tensor_checks(g):
+    n = (4, 3, 2)
+    desc = g.make_desc(n, (2e-9, 2e-9, 2e-9), 8e5)
+    N6 = _sparse_tensor(n, 0.3, 0.3, 0.4, 0.1, 0.1)
+    bad = N6.copy()
+    bad[3, 1, 2, 4] = -bad[3, 1, 2, 4] + 0.01        # breaks the oddness of xy in X
+    with pytest.raises(g.GbdError) as ei:
+        g.gbd_kernel_spectrum_from_tensor_host(desc, bad)
+    assert ei.value.status == g.GBD_EINVAL
+    bad = N6.copy()
+    bad[0, 0, 0, 0] = np.nan
+    with pytest.raises(g.GbdError) as ei:
+        g.gbd_kernel_spectrum_from_tensor_host(desc, bad)
+    assert ei.value.status == g.GBD_EINVAL
+    bad = N6.copy()
+    bad[3, 1, 2, 3] = 0.2                             # xy must vanish at X = 0
+    bad[3, 1, 0, 3] = -0.2
+    bad[3, 1, 4, 3] = 0.2
+    with pytest.raises(g.GbdError):
+        g.gbd_kernel_spectrum_from_tensor_host(desc, bad)
+    with pytest.raises(ValueError):
+        g.gbd_kernel_spectrum_from_tensor_host(desc, N6[:, :, :, :-1])
