@@ -67,6 +67,7 @@ struct RowArgs {
   float hx, hy, hz;         // applied field, A/m
   float geff, alpha;        // gamma / (1 + alpha^2), alpha
   float dt;                 // time step, s
+  int vec8;                 // the field pointers allow 8-byte accesses (set by launch_row)
 };
 
 struct ColArgs {

@@ -2,6 +2,7 @@
 // steps of Appendix A with one GPU) with the fused exchange (Eq. 4) + LLG (Eq. 5) + RK4
 // epilogue (Sec. III). The inverse x transform, the epilogue and the next stage's forward
 // x transform run in one launch on RB rows per block.
+#include <cstdint>
 #include <mutex>
 #include <set>
 #include <utility>
@@ -191,10 +192,10 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
     };
     const bool need_m0 = (mode == ROW_RK2 || mode == ROW_RK3 || mode == ROW_RK4);
     const long long sz = (long long)nx * ny;
-    if ((nx % 64) == 0) {
-      // Fast path: an item is a pair of cells (x0, x0 + 1); the 32 lanes of a warp take 32
-      // consecutive pairs of one row, so the x neighbours outside a pair come from the
-      // adjacent lanes. Loads and stores are 8-byte vectors.
+    if ((nx % 64) == 0 && a.vec8) {
+      // Fast path (8-byte aligned fields): an item is a pair of cells (x0, x0 + 1); the 32
+      // lanes of a warp take 32 consecutive pairs of one row, so the x neighbours outside a
+      // pair come from the adjacent lanes. Loads and stores are 8-byte vectors.
       const int NP2 = nx / 2;
       for (int e = threadIdx.x; e < RB * NP2; e += T) {
         const int rr = e / NP2;
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
     // are one complex slot, read as 8-byte vectors when nx is even
     constexpr int PAIRS = LINES * (FL / 2);
     constexpr int IPT = (PAIRS + T - 1) / T;
-    if (FL >= 2 && (nx % 2) == 0) {
+    if (FL >= 2 && (nx % 2) == 0 && a.vec8) {
       float2 v[IPT];
 #pragma unroll
       for (int i = 0; i < IPT; ++i) {
@@ -469,7 +470,12 @@ static bool row_dispatch(int Lx, int var, int prec, const RowArgs* a, const floa
   }
 }
 
-bool launch_row(int Lx, int var, int prec, const RowArgs& a, const float2* tw, cudaStream_t st) {
+// The caller's fields need only 4-byte alignment; the 8-byte vector paths are enabled here,
+// per launch, from the actual pointers.
+bool launch_row(int Lx, int var, int prec, const RowArgs& a0, const float2* tw, cudaStream_t st) {
+  RowArgs a = a0;
+  auto al8 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; };
+  a.vec8 = (al8(a.in) && al8(a.ms) && al8(a.m0) && al8(a.m0_out) && al8(a.acc) && al8(a.mnext) && al8(a.out)) ? 1 : 0;
   return row_dispatch(Lx, var, prec, &a, tw, st);
 }
 bool prepare_row(int Lx, int prec) { return row_dispatch(Lx, -1, prec, nullptr, nullptr, nullptr); }
