@@ -247,6 +247,32 @@ def run_ours(args):
                 "passes_us": {k: round(v[0] / v[1] * 1e3, 2) for k, v in passes.items()},
                 "share": {k: round(v[0] / sum(x[0] for x in passes.values()), 3) for k, v in passes.items()}}
 
+    # the same run with the demag extrapolated at RK4 sub-steps (Sec. III; one demag evaluation
+    # per step after four start-up steps), timed alike, and its end state against the exact run's
+    extrap = None
+    if not args.no_extrap:
+        mx = torch.from_numpy(m0).cuda()
+        mesh.llg_step(mx, nsteps, spec.dt, extrap=True)
+        xt = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mesh.llg_step(mx, nsteps, spec.dt, extrap=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            xt.append(e0.elapsed_time(e1) / 1e3)
+        xt_max = replicas.max_over_ranks(sum(xt), "cuda")
+        a_, b_ = torch.from_numpy(m0).cuda(), torch.from_numpy(m0).cuda()
+        mesh.llg_step(a_, nsteps, spec.dt)
+        mesh.llg_step(b_, nsteps, spec.dt, extrap=True)
+        evals = 4 * min(nsteps, 4) + max(nsteps - 4, 0)
+        extrap = {"llg_steps_per_s": round(world * nsteps * args.steps / xt_max, 1),
+                  "speedup_vs_exact_steps": round(t_total / xt_max, 3),
+                  "demag_evals_per_llg_step": round(evals / nsteps, 4),
+                  "gcell_demag_per_s": round(world * cells * evals * args.steps / xt_max / 1e9, 3),
+                  "max_abs_dm_vs_exact_after_%d_steps" % nsteps: float((a_ - b_).abs().max())}
+
     result = None
     if rank == 0:
         result = {
@@ -264,6 +290,8 @@ def run_ours(args):
             "clocks": clocks,
             "roofline": roofline,
         }
+        if extrap is not None:
+            result["extrapolated_demag"] = extrap
         if world == 1 and not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(spec, m0, repeats=4)
     mesh.close()
@@ -597,6 +625,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--llg-steps", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extrap", action="store_true", help="skip the demag-extrapolation run of the film")
     ap.add_argument("--workload", default="film", choices=["film", "batch", "serve", "3d", "cufft"])
     ap.add_argument("--oracle-3d", action="store_true", help="3d: FP64 oracle of the full mesh (minutes, ~30 GB)")
     ap.add_argument("--batch-count", type=int, default=64)

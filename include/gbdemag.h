@@ -117,6 +117,23 @@ gbd_status gbd_llg_rhs(gbd_mesh* mesh, const float* m, float* dmdt, void* stream
  * each step. m: device [3][nz][ny][nx] float32 unit vectors. nsteps = 0 is a no-op. */
 gbd_status gbd_llg_step(gbd_mesh* mesh, float* m, int nsteps, double dt, void* stream);
 
+/* gbd_llg_step with options. flags = 0 is gbd_llg_step.
+ * GBD_STEP_EXTRAP: demag extrapolation at RK4 sub-steps (Sec. III: one demag evaluation per
+ *   step, the other stages from a quartic polynomial in time). The demag field is evaluated at
+ *   the first stage of each step and kept in a five-entry history; once the history holds the
+ *   four previous step starts, stages 2 and 3 (t + dt/2) and 4 (t + dt) take the Lagrange
+ *   quartic through the last five step-start fields instead of an evaluation (exchange and
+ *   Zeeman fields are still evaluated). The first four steps of a run evaluate every stage.
+ *   The mesh allocates the history (60 bytes per cell, not counted by gbd_mesh_bytes) on the
+ *   first such call; GBD_ENOMEM if it cannot.
+ * GBD_STEP_CONTINUE (with GBD_STEP_EXTRAP): keep the history of the previous call, so no new
+ *   start-up; valid only when m is that call's result, unchanged, and dt is the same (a
+ *   different dt restarts the history). Without it every call starts a new history.
+ * Other bits: GBD_EINVAL. */
+#define GBD_STEP_EXTRAP 1u
+#define GBD_STEP_CONTINUE 2u
+gbd_status gbd_llg_step_ex(gbd_mesh* mesh, float* m, int nsteps, double dt, unsigned flags, void* stream);
+
 /* ---- allocation-free demag --------------------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that cannot call
  * cudaMalloc at the moment they need the field -- for example code embedded in a host

@@ -43,6 +43,11 @@ struct gbd_mesh {
   float* bufA = nullptr;
   float* bufB = nullptr;
   float2* tw = nullptr;     // twiddle levels, 2 GBD_TW_LEN entries
+  // demag history for extrapolation at RK4 sub-steps: 5 slots of [3][N], allocated on the
+  // first gbd_llg_step_ex with GBD_STEP_EXTRAP; hist_head = newest slot
+  float* hist = nullptr;
+  int hist_count = 0, hist_head = 0;
+  double hist_dt = 0.0;
   bool kernel_set = false;
   // optional per-launch timing: events[2i], events[2i+1] bracket launch i of class cls[i]
   bool timing = false;
@@ -159,6 +164,8 @@ static void free_mesh_buffers(gbd_mesh* m) {
   cudaFree(m->bufA);
   cudaFree(m->bufB);
   cudaFree(m->tw);
+  cudaFree(m->hist);
+  m->hist = nullptr;
   m->S = m->T = nullptr;
   m->K = nullptr;
   m->acc = m->bufA = m->bufB = nullptr;
@@ -591,13 +598,46 @@ gbd_status gbd_llg_rhs(gbd_mesh* m, const float* mm, float* dmdt, void* stream) 
   return field_like(m, mm, dmdt, gbd::ROW_RHS, stream, "gbd_llg_rhs");
 }
 
-gbd_status gbd_llg_step(gbd_mesh* m, float* mm, int nsteps, double dt, void* stream) {
+// Lagrange weights of the quartic through the step starts t_n, t_n - dt, ..., t_n - 4 dt,
+// evaluated at t_n + c dt.
+static void extrap_weights(double c, float w[5]) {
+  for (int k = 0; k < 5; ++k) {
+    double num = 1.0, den = 1.0;
+    for (int j = 0; j < 5; ++j)
+      if (j != k) {
+        num *= c + j;
+        den *= (double)(j - k);
+      }
+    w[k] = (float)(num / den);
+  }
+}
+
+gbd_status gbd_llg_step_ex(gbd_mesh* m, float* mm, int nsteps, double dt, unsigned flags, void* stream) {
   gbd_status s = ready(m);
   if (s != GBD_OK) return s;
   if (!ptr_ok(mm)) return fail(GBD_EINVAL, "m must be a non-NULL, 4-byte aligned device pointer");
   if (nsteps < 0) return fail(GBD_EINVAL, "nsteps must be >= 0");
   if (!(dt > 0) || !std::isfinite(dt)) return fail(GBD_EINVAL, "dt must be finite and > 0");
+  if (flags & ~(unsigned)(GBD_STEP_EXTRAP | GBD_STEP_CONTINUE)) return fail(GBD_EINVAL, "unknown flags");
   if (nsteps == 0) return GBD_OK;
+  const bool extrap = (flags & GBD_STEP_EXTRAP) != 0;
+  const long long n3 = 3 * m->p.N;
+  if (extrap) {
+    if (!m->hist) {
+      cudaError_t e = cudaMalloc(&m->hist, (size_t)5 * n3 * sizeof(float));
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        m->hist = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? GBD_ENOMEM : GBD_ECUDA, "demag history allocation");
+      }
+      m->hist_count = 0;
+    }
+    if (!(flags & GBD_STEP_CONTINUE) || dt != m->hist_dt) m->hist_count = 0;
+    m->hist_dt = dt;
+  }
+  float w_half[5], w_one[5];
+  extrap_weights(0.5, w_half);
+  extrap_weights(1.0, w_one);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   gbd::RowArgs a = row_args(m);
   a.dt = (float)dt;
@@ -613,16 +653,40 @@ gbd_status gbd_llg_step(gbd_mesh* m, float* mm, int nsteps, double dt, void* str
     // stage inputs: m -> A -> B -> A -> m
     const float* ms[4] = {mm, m->bufA, m->bufB, m->bufA};
     float* mn[4] = {m->bufA, m->bufB, m->bufA, nullptr};
+    // with four earlier step-start fields in the history, this step's stages 2-4 extrapolate
+    const bool warm = extrap && m->hist_count >= 4;
     for (int stage = 0; stage < 4; ++stage) {
-      enqueue_conv(m, st);
       a.ms = ms[stage];
       a.mnext = mn[stage];
       a.mode = gbd::ROW_RK1 + stage;
-      a.fwd_after = (last && stage == 3) ? 0 : 1;
+      a.extrap = 0;
+      a.hrec = nullptr;
+      if (stage == 0 && extrap) {
+        m->hist_head = (m->hist_head + 1) % 5;
+        a.hrec = m->hist + (size_t)m->hist_head * n3;
+        if (m->hist_count < 5) ++m->hist_count;
+      }
+      if (warm && stage > 0) {
+        a.extrap = 1;
+        const float* w = (stage == 3) ? w_one : w_half;
+        for (int k = 0; k < 5; ++k) {
+          a.hw[k] = w[k];
+          a.hist[k] = m->hist + (size_t)((m->hist_head - k + 5) % 5) * n3;
+        }
+      } else {
+        enqueue_conv(m, st);
+      }
+      // the next stage needs this stage's forward transform unless it extrapolates
+      const bool next_exact = stage == 3 ? !last : !warm;
+      a.fwd_after = next_exact ? 1 : 0;
       timed(m, GBD_PASS_ROW_RK, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
     }
   }
   return after_launch("gbd_llg_step");
+}
+
+gbd_status gbd_llg_step(gbd_mesh* m, float* mm, int nsteps, double dt, void* stream) {
+  return gbd_llg_step_ex(m, mm, nsteps, dt, 0u, stream);
 }
 
 }  // extern "C"

@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
   const bool vec = (VR == 2) && one_plane && (ny % 2 == 0);
 
   if (mode != ROW_FWD) {
+    if (!a.extrap) {  // uniform over the grid
     // 1. X (global, [kx][y] layout) -> Z pairwise into shared memory. An item is (row group,
     //    component, k) with VR adjacent rows per group, read as one 16-byte vector when the
     //    rows are adjacent in memory; every thread issues all its loads before using any.
@@ -139,6 +140,7 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
       pass_any<PREC, 1, true, LX, radix_at(LX, false, 0), 1, LINES, false, true>(tw, ld, st);
       __syncthreads();
     }
+    }
     // 3. epilogue on the real rows: float view of line position x is 2 pad(x/2) + (x & 1).
     float* __restrict__ out = a.out;
     float* __restrict__ acc = a.acc;
@@ -209,9 +211,22 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
         float hd[2][3], mv[2][3], lap[2][3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const float2 h2 = sm[(c * RB + rr) * LS + pad(xp)];
-          hd[0][c] = h2.x * a.hscale;
-          hd[1][c] = h2.y * a.hscale;
+          if (a.extrap) {
+            float2 h2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+              const float2 hk = *reinterpret_cast<const float2*>(a.hist[k] + c * N + idx);
+              h2.x = fmaf(a.hw[k], hk.x, h2.x);
+              h2.y = fmaf(a.hw[k], hk.y, h2.y);
+            }
+            hd[0][c] = h2.x;
+            hd[1][c] = h2.y;
+          } else {
+            const float2 h2 = sm[(c * RB + rr) * LS + pad(xp)];
+            hd[0][c] = h2.x * a.hscale;
+            hd[1][c] = h2.y * a.hscale;
+          }
+          if (a.hrec) *reinterpret_cast<float2*>(a.hrec + c * N + idx) = make_float2(hd[0][c], hd[1][c]);
         }
         if (mode == ROW_H) {
 #pragma unroll
@@ -282,7 +297,17 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
         const int fpos = 2 * pad(x >> 1) + (x & 1);
         float hd[3], mv[3], lap[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) hd[c] = reinterpret_cast<const float*>(sm + (c * RB + rr) * LS)[fpos] * a.hscale;
+        for (int c = 0; c < 3; ++c) {
+          if (a.extrap) {
+            float h = 0.f;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) h = fmaf(a.hw[k], a.hist[k][c * N + idx], h);
+            hd[c] = h;
+          } else {
+            hd[c] = reinterpret_cast<const float*>(sm + (c * RB + rr) * LS)[fpos] * a.hscale;
+          }
+          if (a.hrec) a.hrec[c * N + idx] = hd[c];
+        }
         if (mode == ROW_H) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) out[c * N + idx] = hd[c];
@@ -475,7 +500,10 @@ static bool row_dispatch(int Lx, int var, int prec, const RowArgs* a, const floa
 bool launch_row(int Lx, int var, int prec, const RowArgs& a0, const float2* tw, cudaStream_t st) {
   RowArgs a = a0;
   auto al8 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; };
-  a.vec8 = (al8(a.in) && al8(a.ms) && al8(a.m0) && al8(a.m0_out) && al8(a.acc) && al8(a.mnext) && al8(a.out)) ? 1 : 0;
+  bool ok = al8(a.in) && al8(a.ms) && al8(a.m0) && al8(a.m0_out) && al8(a.acc) && al8(a.mnext) && al8(a.out) &&
+            al8(a.hrec);
+  for (int k = 0; k < 5; ++k) ok = ok && al8(a.hist[k]);
+  a.vec8 = ok ? 1 : 0;
   return row_dispatch(Lx, var, prec, &a, tw, st);
 }
 bool prepare_row(int Lx, int prec) { return row_dispatch(Lx, -1, prec, nullptr, nullptr, nullptr); }

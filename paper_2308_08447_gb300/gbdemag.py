@@ -48,6 +48,7 @@ _SIG = {
     "gbd_effective_field": [_P, _P, _P, _P],
     "gbd_llg_rhs": [_P, _P, _P, _P],
     "gbd_llg_step": [_P, _P, _I, _D, _P],
+    "gbd_llg_step_ex": [_P, _P, _I, _D, ctypes.c_uint, _P],
     "gbd_mesh_destroy": [_P],
     "gbd_tensor_at": [ctypes.POINTER(gbd_mesh_desc), _I, _I, _I, ctypes.POINTER(_D)],
     "gbd_plan_dims": [ctypes.POINTER(gbd_mesh_desc), ctypes.POINTER(_I)],
@@ -187,6 +188,15 @@ def gbd_llg_step(mesh, m, nsteps, dt, shape, stream=None):
     _check(load().gbd_llg_step(mesh, _field_ptr(m, shape, "m"), int(nsteps), float(dt), _stream_ptr(stream)))
 
 
+GBD_STEP_EXTRAP = 1
+GBD_STEP_CONTINUE = 2
+
+
+def gbd_llg_step_ex(mesh, m, nsteps, dt, flags, shape, stream=None):
+    _check(load().gbd_llg_step_ex(mesh, _field_ptr(m, shape, "m"), int(nsteps), float(dt), int(flags),
+                                  _stream_ptr(stream)))
+
+
 def gbd_mesh_destroy(mesh):
     _check(load().gbd_mesh_destroy(mesh))
 
@@ -299,8 +309,14 @@ class Mesh:
     def llg_rhs(self, m, dmdt, stream=None):
         gbd_llg_rhs(self.handle, m, dmdt, self.shape, stream)
 
-    def llg_step(self, m, nsteps, dt, stream=None):
-        gbd_llg_step(self.handle, m, nsteps, dt, self.shape, stream)
+    def llg_step(self, m, nsteps, dt, stream=None, extrap=False, cont=False):
+        """nsteps RK4 steps; extrap: demag extrapolated at stages 2-4 (GBD_STEP_EXTRAP), cont:
+        continue the previous call's demag history (GBD_STEP_CONTINUE)."""
+        if not extrap and not cont:
+            gbd_llg_step(self.handle, m, nsteps, dt, self.shape, stream)
+        else:
+            flags = (GBD_STEP_EXTRAP if extrap else 0) | (GBD_STEP_CONTINUE if cont else 0)
+            gbd_llg_step_ex(self.handle, m, nsteps, dt, flags, self.shape, stream)
 
     def autotune(self, stream=None):
         gbd_mesh_autotune(self.handle, stream)
