@@ -212,6 +212,7 @@ enum {
   GBD_PASS_Y_FWD = 4,      /* 3D y FFT */
   GBD_PASS_Z_CONV = 5,     /* 3D z FFT -> kernel product -> z IFFT */
   GBD_PASS_Y_INV = 6,      /* 3D y IFFT + crop */
+  GBD_PASS_EXTRAP = 7,     /* extrapolated RK4 stage without a transform (GBD_STEP_EXTRAP) */
   GBD_NPASS = 8
 };
 

@@ -679,7 +679,10 @@ gbd_status gbd_llg_step_ex(gbd_mesh* m, float* mm, int nsteps, double dt, unsign
       // the next stage needs this stage's forward transform unless it extrapolates
       const bool next_exact = stage == 3 ? !last : !warm;
       a.fwd_after = next_exact ? 1 : 0;
-      timed(m, GBD_PASS_ROW_RK, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
+      if (a.extrap && !a.fwd_after)
+        timed(m, GBD_PASS_EXTRAP, st, [&] { gbd::launch_extrap_stage(a, st); });
+      else
+        timed(m, GBD_PASS_ROW_RK, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
     }
   }
   return after_launch("gbd_llg_step");

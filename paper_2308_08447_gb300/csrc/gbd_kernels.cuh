@@ -92,6 +92,9 @@ struct ColArgs {
 // return false for a length without an instantiation.
 // prec: 0 FP32 stages; 1 radix-16 stages on the tensor cores in split BF16 (gbd_tc.cuh).
 bool launch_row(int Lx, int var, int prec, const RowArgs& a, const float2* tw, cudaStream_t st);
+// An extrapolated RK4 stage with no forward transform after it (a.extrap = 1, a.fwd_after = 0):
+// the row kernel's epilogue alone, at full occupancy.
+void launch_extrap_stage(const RowArgs& a, cudaStream_t st);
 bool launch_film_conv(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st);
 bool launch_y_fwd(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st);
 bool launch_y_inv(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st);

@@ -28,6 +28,240 @@ bool prep_seen(const void* k, int dev) {
 // inverse, and the forward reads only those: the upper half is the zero padding.
 // ---------------------------------------------------------------------------------------------
 
+// ---------------------------------------------------------------------------------------------
+// Epilogue of the inverse x transform (Sec. III): exchange field (Eq. 4, 7-point Laplacian with
+// free boundaries), H_eff, the LLG right-hand side (Eq. 5 solved for dm/dt) and the RK4 stage
+// update, per cell, from the demag field hd of the cell.
+// ---------------------------------------------------------------------------------------------
+
+// res = H_eff (ROW_HEFF) or dm/dt (ROW_RHS); in RK4 stages the k-sum in acc_out and the next
+// stage's m in mn. m0v / accv: the cell's step-start m and k-sum (stages 2-4).
+__device__ __forceinline__ void llg_update(const RowArgs& a, int mode, const float* hd, const float* m,
+                                           const float* lap, const float* m0v, const float* accv, float* mn,
+                                           float* acc_out, float* res) {
+  float H[3] = {hd[0] + lap[0] + a.hx, hd[1] + lap[1] + a.hy, hd[2] + lap[2] + a.hz};
+  if (mode == ROW_HEFF) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) res[c] = H[c];
+    return;
+  }
+  // dm/dt = -gamma/(1+alpha^2) [m x H + alpha m x (m x H)]
+  const float mxH[3] = {m[1] * H[2] - m[2] * H[1], m[2] * H[0] - m[0] * H[2], m[0] * H[1] - m[1] * H[0]};
+  const float mmH[3] = {m[1] * mxH[2] - m[2] * mxH[1], m[2] * mxH[0] - m[0] * mxH[2], m[0] * mxH[1] - m[1] * mxH[0]};
+  float f[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) f[c] = -a.geff * (mxH[c] + a.alpha * mmH[c]);
+  if (mode == ROW_RHS) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) res[c] = f[c];
+    return;
+  }
+  if (mode == ROW_RK1) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc_out[c] = f[c];
+      mn[c] = m[c] + 0.5f * a.dt * f[c];
+    }
+  } else if (mode == ROW_RK2 || mode == ROW_RK3) {
+    const float h = (mode == ROW_RK2) ? 0.5f * a.dt : a.dt;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc_out[c] = accv[c] + 2.f * f[c];
+      mn[c] = m0v[c] + h * f[c];
+    }
+  } else {  // ROW_RK4
+    const float h = a.dt * (1.0f / 6.0f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) mn[c] = m0v[c] + h * (accv[c] + f[c]);
+    const float inv = rsqrtf(mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) mn[c] *= inv;
+  }
+}
+
+// Extrapolated demag field (sum_k hw[k] hist[k]) of cells idx, idx + 1.
+__device__ __forceinline__ void extrap_pair(const RowArgs& a, long long idx, float (&hd)[2][3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float2 h2 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const float2 hk = *reinterpret_cast<const float2*>(a.hist[k] + c * a.N + idx);
+      h2.x = fmaf(a.hw[k], hk.x, h2.x);
+      h2.y = fmaf(a.hw[k], hk.y, h2.y);
+    }
+    hd[0][c] = h2.x;
+    hd[1][c] = h2.y;
+  }
+}
+
+__device__ __forceinline__ void extrap_cell(const RowArgs& a, long long idx, float (&hd)[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float h = 0.f;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) h = fmaf(a.hw[k], a.hist[k][c * a.N + idx], h);
+    hd[c] = h;
+  }
+}
+
+// Epilogue of the pair of cells (x0, x0 + 1), x0 even, at linear index idx (row of plane z at
+// y) for nx a multiple of 64 and 8-byte aligned fields: the 32 lanes of the warp hold 32
+// consecutive pairs of the row, so the x neighbours outside a pair come from the adjacent
+// lanes; loads and stores are 8-byte vectors. Records hd when hrec is set, writes the mode's
+// outputs, and returns true with the next stage's m in mn for the RK4 stages.
+__device__ __forceinline__ bool epilogue_pair(const RowArgs& a, int mode, int z, int y, long long idx, int x0,
+                                              int lane, const float (&hd)[2][3], float (&mn)[2][3]) {
+  const long long N = a.N;
+  const int nx = a.nx, ny = a.ny;
+  const long long sz = (long long)nx * ny;
+  if (a.hrec) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) *reinterpret_cast<float2*>(a.hrec + c * N + idx) = make_float2(hd[0][c], hd[1][c]);
+  }
+  if (mode == ROW_H) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) *reinterpret_cast<float2*>(a.out + c * N + idx) = make_float2(hd[0][c], hd[1][c]);
+    return false;
+  }
+  float mv[2][3], lap[2][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float* __restrict__ p = a.ms + c * N + idx;
+    const float2 cc = *reinterpret_cast<const float2*>(p);
+    const float2 ym = y > 0 ? *reinterpret_cast<const float2*>(p - nx) : cc;
+    const float2 yp = y < ny - 1 ? *reinterpret_cast<const float2*>(p + nx) : cc;
+    float2 zm = cc, zp = cc;
+    if (a.nz > 1) {
+      if (z > 0) zm = *reinterpret_cast<const float2*>(p - sz);
+      if (z < a.nz - 1) zp = *reinterpret_cast<const float2*>(p + sz);
+    }
+    float left = __shfl_up_sync(0xffffffffu, cc.y, 1);
+    float right = __shfl_down_sync(0xffffffffu, cc.x, 1);
+    if (lane == 0) left = x0 > 0 ? p[-1] : cc.x;
+    if (lane == 31) right = x0 + 2 < nx ? p[2] : cc.y;
+    mv[0][c] = cc.x;
+    mv[1][c] = cc.y;
+    lap[0][c] = a.cx * (left - 2.f * cc.x + cc.y) + a.cy * (ym.x - 2.f * cc.x + yp.x) + a.cz * (zm.x - 2.f * cc.x + zp.x);
+    lap[1][c] = a.cx * (cc.x - 2.f * cc.y + right) + a.cy * (ym.y - 2.f * cc.y + yp.y) + a.cz * (zm.y - 2.f * cc.y + zp.y);
+  }
+  float m0v[2][3] = {}, accv[2][3] = {};
+  if (mode == ROW_RK2 || mode == ROW_RK3 || mode == ROW_RK4) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float2 q0 = *reinterpret_cast<const float2*>(a.m0 + c * N + idx);
+      const float2 qa = *reinterpret_cast<const float2*>(a.acc + c * N + idx);
+      m0v[0][c] = q0.x;
+      m0v[1][c] = q0.y;
+      accv[0][c] = qa.x;
+      accv[1][c] = qa.y;
+    }
+  }
+  float ao[2][3], res[2][3];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) llg_update(a, mode, hd[u], mv[u], lap[u], m0v[u], accv[u], mn[u], ao[u], res[u]);
+  if (mode == ROW_HEFF || mode == ROW_RHS) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) *reinterpret_cast<float2*>(a.out + c * N + idx) = make_float2(res[0][c], res[1][c]);
+    return false;
+  }
+  // m0_out aliases m0 in stage 4: each cell is read, then written, by one thread
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float2 v = make_float2(mn[0][c], mn[1][c]);
+    if (mode == ROW_RK4) {
+      *reinterpret_cast<float2*>(a.m0_out + c * N + idx) = v;
+    } else {
+      *reinterpret_cast<float2*>(a.acc + c * N + idx) = make_float2(ao[0][c], ao[1][c]);
+      *reinterpret_cast<float2*>(a.mnext + c * N + idx) = v;
+    }
+  }
+  return true;
+}
+
+// The same for one cell at (x, y, z), linear index idx, any nx and 4-byte aligned fields.
+__device__ __forceinline__ bool epilogue_cell(const RowArgs& a, int mode, int z, int y, int x, long long idx,
+                                              const float (&hd)[3], float (&mn)[3]) {
+  const long long N = a.N;
+  const int nx = a.nx, ny = a.ny;
+  const long long sz = (long long)nx * ny;
+  if (a.hrec) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a.hrec[c * N + idx] = hd[c];
+  }
+  if (mode == ROW_H) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a.out[c * N + idx] = hd[c];
+    return false;
+  }
+  // exchange: 7-point Laplacian, free boundaries (missing neighbour = the cell itself)
+  const long long ixm = x > 0 ? idx - 1 : idx, ixp = x < nx - 1 ? idx + 1 : idx;
+  const long long iym = y > 0 ? idx - nx : idx, iyp = y < ny - 1 ? idx + nx : idx;
+  const long long izm = z > 0 ? idx - sz : idx, izp = z < a.nz - 1 ? idx + sz : idx;
+  float mv[3], lap[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float* __restrict__ p = a.ms + c * N;
+    const float mc = p[idx];
+    mv[c] = mc;
+    lap[c] = a.cx * (p[ixp] - 2.f * mc + p[ixm]) + a.cy * (p[iyp] - 2.f * mc + p[iym]) +
+             a.cz * (p[izp] - 2.f * mc + p[izm]);
+  }
+  float m0v[3] = {}, accv[3] = {};
+  if (mode == ROW_RK2 || mode == ROW_RK3 || mode == ROW_RK4) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      m0v[c] = a.m0[c * N + idx];
+      accv[c] = a.acc[c * N + idx];
+    }
+  }
+  float ao[3], res[3];
+  llg_update(a, mode, hd, mv, lap, m0v, accv, mn, ao, res);
+  if (mode == ROW_HEFF || mode == ROW_RHS) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a.out[c * N + idx] = res[c];
+    return false;
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (mode == ROW_RK4) {
+      a.m0_out[c * N + idx] = mn[c];
+    } else {
+      a.acc[c * N + idx] = ao[c];
+      a.mnext[c * N + idx] = mn[c];
+    }
+  }
+  return true;
+}
+
+// Extrapolated RK4 stage without a transform (stages 2 and 3, and a last stage 4): the
+// epilogue alone over all cells, the demag field from the history. One thread per pair of
+// cells (nx % 64 == 0, 8-byte aligned fields) or per cell.
+__global__ void __launch_bounds__(256) extrap_stage_kernel(const RowArgs a) {
+  const int nx = a.nx, ny = a.ny;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((nx % 64) == 0 && a.vec8) {
+    // items in a warp are 32 consecutive pairs of one row: nx / 2 and 256 are multiples of 32
+    const int NP2 = nx / 2;
+    if (i >= (long long)a.rows * NP2) return;
+    const int row = (int)(i / NP2);
+    const int xp = (int)(i - (long long)row * NP2);
+    const int z = row / ny, y = row - z * ny;
+    const long long idx = (long long)row * nx + 2 * xp;
+    float hd[2][3], mn[2][3];
+    extrap_pair(a, idx, hd);
+    epilogue_pair(a, a.mode, z, y, idx, 2 * xp, threadIdx.x & 31, hd, mn);
+  } else {
+    if (i >= a.N) return;
+    const int row = (int)(i / nx);
+    const int x = (int)(i - (long long)row * nx);
+    const int z = row / ny, y = row - z * ny;
+    float hd[3], mn[3];
+    extrap_cell(a, i, hd);
+    epilogue_cell(a, a.mode, z, y, x, i, hd, mn);
+  }
+}
+
 template <int LX, int RB_, int PREC>
 __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX / GBD_E))
     row_kernel(RowArgs a, const float2* __restrict__ tw) {
@@ -142,62 +376,9 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
     }
     }
     // 3. epilogue on the real rows: float view of line position x is 2 pad(x/2) + (x & 1).
-    float* __restrict__ out = a.out;
-    float* __restrict__ acc = a.acc;
-    float* __restrict__ mnext = a.mnext;
-    const float* __restrict__ m0 = a.m0;
-    float* __restrict__ m0_out = a.m0_out;  // aliases m0 in stage 4: each cell is read, then written, by one thread
-    // Per-cell update from the demag field hd, m and its Laplacian lap; m0v / accv are the
-    // cell's step-start m and k-sum (read only by the stages that need them). Returns the
-    // next stage's m in mn (stages) and writes the mode's global outputs through `put`.
-    auto update = [&](const float* hd, const float* m, const float* lap, const float* m0v, const float* accv,
-                      float* mn, float* acc_out, float* res) {
-      float H[3] = {hd[0] + lap[0] + a.hx, hd[1] + lap[1] + a.hy, hd[2] + lap[2] + a.hz};
-      if (mode == ROW_HEFF) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) res[c] = H[c];
-        return;
-      }
-      // dm/dt = -gamma/(1+alpha^2) [m x H + alpha m x (m x H)]
-      const float mxH[3] = {m[1] * H[2] - m[2] * H[1], m[2] * H[0] - m[0] * H[2], m[0] * H[1] - m[1] * H[0]};
-      const float mmH[3] = {m[1] * mxH[2] - m[2] * mxH[1], m[2] * mxH[0] - m[0] * mxH[2],
-                            m[0] * mxH[1] - m[1] * mxH[0]};
-      float f[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) f[c] = -a.geff * (mxH[c] + a.alpha * mmH[c]);
-      if (mode == ROW_RHS) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) res[c] = f[c];
-        return;
-      }
-      if (mode == ROW_RK1) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          acc_out[c] = f[c];
-          mn[c] = m[c] + 0.5f * a.dt * f[c];
-        }
-      } else if (mode == ROW_RK2 || mode == ROW_RK3) {
-        const float h = (mode == ROW_RK2) ? 0.5f * a.dt : a.dt;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          acc_out[c] = accv[c] + 2.f * f[c];
-          mn[c] = m0v[c] + h * f[c];
-        }
-      } else {  // ROW_RK4
-        const float h = a.dt * (1.0f / 6.0f);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) mn[c] = m0v[c] + h * (accv[c] + f[c]);
-        const float inv = rsqrtf(mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) mn[c] *= inv;
-      }
-    };
-    const bool need_m0 = (mode == ROW_RK2 || mode == ROW_RK3 || mode == ROW_RK4);
-    const long long sz = (long long)nx * ny;
     if ((nx % 64) == 0 && a.vec8) {
       // Fast path (8-byte aligned fields): an item is a pair of cells (x0, x0 + 1); the 32
-      // lanes of a warp take 32 consecutive pairs of one row, so the x neighbours outside a
-      // pair come from the adjacent lanes. Loads and stores are 8-byte vectors.
+      // lanes of a warp take 32 consecutive pairs of one row (epilogue_pair).
       const int NP2 = nx / 2;
       for (int e = threadIdx.x; e < RB * NP2; e += T) {
         const int rr = e / NP2;
@@ -207,86 +388,24 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
         row_zy(rr, z, y);
         const int x0 = 2 * xp;
         const long long idx = (long long)(r0 + rr) * nx + x0;
-        const int lane = threadIdx.x & 31;
-        float hd[2][3], mv[2][3], lap[2][3];
+        float hd[2][3], mn[2][3];
+        if (a.extrap) {
+          extrap_pair(a, idx, hd);
+        } else {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          if (a.extrap) {
-            float2 h2 = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int k = 0; k < 5; ++k) {
-              const float2 hk = *reinterpret_cast<const float2*>(a.hist[k] + c * N + idx);
-              h2.x = fmaf(a.hw[k], hk.x, h2.x);
-              h2.y = fmaf(a.hw[k], hk.y, h2.y);
-            }
-            hd[0][c] = h2.x;
-            hd[1][c] = h2.y;
-          } else {
+          for (int c = 0; c < 3; ++c) {
             const float2 h2 = sm[(c * RB + rr) * LS + pad(xp)];
             hd[0][c] = h2.x * a.hscale;
             hd[1][c] = h2.y * a.hscale;
           }
-          if (a.hrec) *reinterpret_cast<float2*>(a.hrec + c * N + idx) = make_float2(hd[0][c], hd[1][c]);
         }
-        if (mode == ROW_H) {
+        if (epilogue_pair(a, mode, z, y, idx, x0, threadIdx.x & 31, hd, mn) && a.fwd_after) {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) *reinterpret_cast<float2*>(out + c * N + idx) = make_float2(hd[0][c], hd[1][c]);
-          continue;
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float* __restrict__ p = ms + c * N + idx;
-          const float2 cc = *reinterpret_cast<const float2*>(p);
-          const float2 ym = y > 0 ? *reinterpret_cast<const float2*>(p - nx) : cc;
-          const float2 yp = y < ny - 1 ? *reinterpret_cast<const float2*>(p + nx) : cc;
-          float2 zm = cc, zp = cc;
-          if (a.nz > 1) {
-            if (z > 0) zm = *reinterpret_cast<const float2*>(p - sz);
-            if (z < a.nz - 1) zp = *reinterpret_cast<const float2*>(p + sz);
-          }
-          float left = __shfl_up_sync(0xffffffffu, cc.y, 1);
-          float right = __shfl_down_sync(0xffffffffu, cc.x, 1);
-          if (lane == 0) left = x0 > 0 ? p[-1] : cc.x;
-          if (lane == 31) right = x0 + 2 < nx ? p[2] : cc.y;
-          mv[0][c] = cc.x;
-          mv[1][c] = cc.y;
-          lap[0][c] = a.cx * (left - 2.f * cc.x + cc.y) + a.cy * (ym.x - 2.f * cc.x + yp.x) + a.cz * (zm.x - 2.f * cc.x + zp.x);
-          lap[1][c] = a.cx * (cc.x - 2.f * cc.y + right) + a.cy * (ym.y - 2.f * cc.y + yp.y) + a.cz * (zm.y - 2.f * cc.y + zp.y);
-        }
-        float m0v[2][3] = {}, accv[2][3] = {};
-        if (need_m0) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float2 q0 = *reinterpret_cast<const float2*>(m0 + c * N + idx);
-            const float2 qa = *reinterpret_cast<const float2*>(acc + c * N + idx);
-            m0v[0][c] = q0.x;
-            m0v[1][c] = q0.y;
-            accv[0][c] = qa.x;
-            accv[1][c] = qa.y;
-          }
-        }
-        float mn[2][3], ao[2][3], res[2][3];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) update(hd[u], mv[u], lap[u], m0v[u], accv[u], mn[u], ao[u], res[u]);
-        if (mode == ROW_HEFF || mode == ROW_RHS) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) *reinterpret_cast<float2*>(out + c * N + idx) = make_float2(res[0][c], res[1][c]);
-          continue;
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float2 v = make_float2(mn[0][c], mn[1][c]);
-          if (mode == ROW_RK4) {
-            *reinterpret_cast<float2*>(m0_out + c * N + idx) = v;
-          } else {
-            *reinterpret_cast<float2*>(acc + c * N + idx) = make_float2(ao[0][c], ao[1][c]);
-            *reinterpret_cast<float2*>(mnext + c * N + idx) = v;
-          }
-          if (a.fwd_after) sm[(c * RB + rr) * LS + pad(xp)] = v;
+          for (int c = 0; c < 3; ++c) sm[(c * RB + rr) * LS + pad(xp)] = make_float2(mn[0][c], mn[1][c]);
         }
       }
     } else {
-      // General path: one cell per item.
+      // General path: one cell per item (epilogue_cell).
       for (int e = threadIdx.x; e < RB * nx; e += T) {
         const int rr = e / nx;
         const int x = e - rr * nx;
@@ -295,60 +414,16 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
         row_zy(rr, z, y);
         const long long idx = (long long)(r0 + rr) * nx + x;
         const int fpos = 2 * pad(x >> 1) + (x & 1);
-        float hd[3], mv[3], lap[3];
+        float hd[3], mn[3];
+        if (a.extrap) {
+          extrap_cell(a, idx, hd);
+        } else {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          if (a.extrap) {
-            float h = 0.f;
-#pragma unroll
-            for (int k = 0; k < 5; ++k) h = fmaf(a.hw[k], a.hist[k][c * N + idx], h);
-            hd[c] = h;
-          } else {
-            hd[c] = reinterpret_cast<const float*>(sm + (c * RB + rr) * LS)[fpos] * a.hscale;
-          }
-          if (a.hrec) a.hrec[c * N + idx] = hd[c];
+          for (int c = 0; c < 3; ++c) hd[c] = reinterpret_cast<const float*>(sm + (c * RB + rr) * LS)[fpos] * a.hscale;
         }
-        if (mode == ROW_H) {
+        if (epilogue_cell(a, mode, z, y, x, idx, hd, mn) && a.fwd_after) {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) out[c * N + idx] = hd[c];
-          continue;
-        }
-        // exchange: 7-point Laplacian, free boundaries (missing neighbour = the cell itself)
-        const long long ixm = x > 0 ? idx - 1 : idx, ixp = x < nx - 1 ? idx + 1 : idx;
-        const long long iym = y > 0 ? idx - nx : idx, iyp = y < ny - 1 ? idx + nx : idx;
-        const long long izm = z > 0 ? idx - sz : idx, izp = z < a.nz - 1 ? idx + sz : idx;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float* __restrict__ p = ms + c * N;
-          const float mc = p[idx];
-          mv[c] = mc;
-          lap[c] = a.cx * (p[ixp] - 2.f * mc + p[ixm]) + a.cy * (p[iyp] - 2.f * mc + p[iym]) +
-                   a.cz * (p[izp] - 2.f * mc + p[izm]);
-        }
-        float m0v[3] = {}, accv[3] = {};
-        if (need_m0) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            m0v[c] = m0[c * N + idx];
-            accv[c] = acc[c * N + idx];
-          }
-        }
-        float mn[3], ao[3], res[3];
-        update(hd, mv, lap, m0v, accv, mn, ao, res);
-        if (mode == ROW_HEFF || mode == ROW_RHS) {
-#pragma unroll
-          for (int c = 0; c < 3; ++c) out[c * N + idx] = res[c];
-          continue;
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          if (mode == ROW_RK4) {
-            m0_out[c * N + idx] = mn[c];
-          } else {
-            acc[c * N + idx] = ao[c];
-            mnext[c * N + idx] = mn[c];
-          }
-          if (a.fwd_after) reinterpret_cast<float*>(sm + (c * RB + rr) * LS)[fpos] = mn[c];
+          for (int c = 0; c < 3; ++c) reinterpret_cast<float*>(sm + (c * RB + rr) * LS)[fpos] = mn[c];
         }
       }
     }
@@ -495,16 +570,27 @@ static bool row_dispatch(int Lx, int var, int prec, const RowArgs* a, const floa
   }
 }
 
-// The caller's fields need only 4-byte alignment; the 8-byte vector paths are enabled here,
-// per launch, from the actual pointers.
-bool launch_row(int Lx, int var, int prec, const RowArgs& a0, const float2* tw, cudaStream_t st) {
-  RowArgs a = a0;
+// The caller's fields need only 4-byte alignment; the 8-byte vector paths are enabled per
+// launch from the actual pointers.
+static void set_vec8(RowArgs& a) {
   auto al8 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; };
   bool ok = al8(a.in) && al8(a.ms) && al8(a.m0) && al8(a.m0_out) && al8(a.acc) && al8(a.mnext) && al8(a.out) &&
             al8(a.hrec);
   for (int k = 0; k < 5; ++k) ok = ok && al8(a.hist[k]);
   a.vec8 = ok ? 1 : 0;
+}
+
+bool launch_row(int Lx, int var, int prec, const RowArgs& a0, const float2* tw, cudaStream_t st) {
+  RowArgs a = a0;
+  set_vec8(a);
   return row_dispatch(Lx, var, prec, &a, tw, st);
+}
+
+void launch_extrap_stage(const RowArgs& a0, cudaStream_t st) {
+  RowArgs a = a0;
+  set_vec8(a);
+  const long long items = ((a.nx % 64) == 0 && a.vec8) ? (long long)a.rows * (a.nx / 2) : a.N;
+  extrap_stage_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(a);
 }
 bool prepare_row(int Lx, int prec) { return row_dispatch(Lx, -1, prec, nullptr, nullptr, nullptr); }
 

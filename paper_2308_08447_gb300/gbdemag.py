@@ -65,7 +65,7 @@ _SIG = {
     "gbd_mesh_set_timing": [_P, _I],
     "gbd_mesh_read_timing": [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)],
 }
-PASS_NAMES = ["row_fwd", "row_inv", "row_rk", "film_conv", "y_fwd", "z_conv", "y_inv", "unused"]
+PASS_NAMES = ["row_fwd", "row_inv", "row_rk", "film_conv", "y_fwd", "z_conv", "y_inv", "extrap_stage"]
 GBD_NPASS = 8
 
 
