@@ -118,6 +118,20 @@ def film_bytes_per_launch(n, Hx, Ky):
     }
 
 
+def bytes_per_pass_3d(n, dims):
+    """Algorithmic DRAM bytes of each pass of one 3D demag evaluation (FP32 fields, complex64
+    spectra): x R2C reads M 12 B/cell, writes S [3][nz][Hx][ny]; y_fwd reads S, writes T
+    [3][nz][Hx][Py]; z_conv reads and writes T and reads the kernel [Hx][Py/2+1][Pz/2+1][6];
+    y_inv reads T, writes S; x C2R reads S and writes H 12 B/cell."""
+    nx, ny, nz = n
+    Px, Py, Pz, Hx, Ky, Kz = dims
+    N = nx * ny * nz
+    S = 24 * Hx * ny * nz
+    Tb = 24 * Hx * Py * nz
+    K = 24 * Hx * Ky * Kz
+    return {"row_fwd": 12 * N + S, "y_fwd": S + Tb, "z_conv": 2 * Tb + K, "y_inv": Tb + S, "row_inv": S + 12 * N}
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -480,6 +494,20 @@ def run_3d(args):
         e1.record(stream)
         torch.cuda.synchronize()
         t_demag = e0.elapsed_time(e1) / 1e3 / args.steps
+        # per-pass device time of one evaluation (events around every launch) against the
+        # algorithmic bytes of each pass
+        gbdemag.gbd_mesh_set_timing(mesh.handle, True)
+        mesh.demag(M, Hd)
+        torch.cuda.synchronize()
+        passes = gbdemag.gbd_mesh_read_timing(mesh.handle)
+        gbdemag.gbd_mesh_set_timing(mesh.handle, False)
+        dims = gbdemag.gbd_plan_dims(mesh.desc)
+        bpp = bytes_per_pass_3d(spec.n, dims)
+        peak, _ = measured_peaks()
+        pass_info = {k: {"us": round(v[0] / v[1] * 1e3, 1), "algorithmic_MB": round(bpp[k] / 1e6, 1),
+                         "GBps": round(bpp[k] / (v[0] / v[1] * 1e-3) / 1e9, 1),
+                         "frac_of_hbm": round(bpp[k] / (v[0] / v[1] * 1e-3) / 1e9 / peak, 3)}
+                     for k, v in passes.items() if k in bpp}
         H[name] = Hd.cpu().numpy()
         m = torch.from_numpy(m0).cuda()
         mesh.llg_step(m, 2, spec.dt)
@@ -492,7 +520,7 @@ def run_3d(args):
         res[name] = {"demag_ms": round(t_demag * 1e3, 3), "demag_gcell_per_s": round(spec.cells / t_demag / 1e9, 3),
                      "llg_100_steps_s": round(t_llg, 4),
                      "llg_gcell_demag_per_s": round(spec.cells * 4 * nsteps / t_llg / 1e9, 3),
-                     "tuning": list(gbdemag.gbd_mesh_get_tuning(mesh.handle))}
+                     "tuning": list(gbdemag.gbd_mesh_get_tuning(mesh.handle)), "passes": pass_info}
         res[name + "_m_after_100"] = m.cpu().numpy()
         mesh.close()
     d = res.pop("split_bf16_m_after_100") - res.pop("fp32_m_after_100")
@@ -593,6 +621,77 @@ def run_cufft(args):
             "speedup_vs_cufft": round(t_cufft / t_ours, 3), "e_inf_ours_vs_cufft": e}
 
 
+def run_switching(args):
+    """The switching problem of Fig. 2 (Sec. II), 480 x 240 x 2 cells of 5 nm: S state by the
+    stated relax protocol, then 1 ns under H = (-20, 1, 0) kA/m with <m> recorded every 10 ps,
+    at several time steps, exact and with the demag extrapolated at RK4 sub-steps. The error of
+    each run is the paper's mean relative error eps = sum_i |M(t_i) - M_ref(t_i)| / (n Ms)
+    against the 25 fs exact run (all FP32 on this GPU); throughput is taken on the 100 fs run."""
+    import numpy as np
+    import torch
+
+    from paper_2308_08447_gb300 import gbdemag
+    from paper_2308_08447_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    gbdemag.load()
+    spec = W.switching()
+    meta = spec.meta
+    mesh = gbdemag.Mesh(spec.n, spec.cell, spec.Ms, A_ex=spec.A_ex, alpha=meta["relax_alpha"])
+    mesh.autotune()
+    stream = torch.cuda.current_stream()
+    m = torch.from_numpy(W.uniform(spec.n, meta["m_init"])).cuda()
+    t0 = time.perf_counter()
+    dt_relax = 1e-13
+    for h in meta["relax_fields"]:
+        mesh.set_params(Hext=tuple(h * c for c in meta["relax_dir"]), alpha=meta["relax_alpha"])
+        mesh.llg_step(m, int(round(meta["relax_hold"] / dt_relax)), dt_relax)
+    torch.cuda.synchronize()
+    relax_s = time.perf_counter() - t0
+    mS = m.clone()
+    mesh.set_params(Hext=spec.Hext, alpha=spec.alpha)
+    interval, t_end = 10e-12, meta["t_switch"]
+    n_rec = int(round(t_end / interval))
+
+    def run(dt, extrap):
+        mm = mS.clone()
+        per = int(round(interval / dt))
+        rec = []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(n_rec):
+            mesh.llg_step(mm, per, dt, extrap=extrap, cont=extrap and i > 0)
+            rec.append(mm.mean(dim=(1, 2, 3)))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return torch.stack(rec).double().cpu().numpy(), e0.elapsed_time(e1) / 1e3, per * n_rec
+
+    ref, _, _ = run(25e-15, False)
+    scaling = {}
+    timing = {}
+    for dt in (400e-15, 200e-15, 100e-15, 50e-15):
+        row = {}
+        for extrap in (False, True):
+            traj, secs, steps = run(dt, extrap)
+            row["extrap" if extrap else "exact"] = float(np.linalg.norm(traj - ref, axis=1).sum() / n_rec)
+            timing[(dt, extrap)] = (secs, steps)
+        scaling["%g fs" % (dt * 1e15)] = row
+    secs, steps = timing[(100e-15, False)]
+    xsecs, xsteps = timing[(100e-15, True)]
+    mesh.close()
+    samples = {"%g ns" % (t * 1e9): [round(float(v), 5) for v in ref[int(round(t / interval)) - 1]]
+               for t in (0.1e-9, 0.25e-9, 0.5e-9, 0.75e-9, 1e-9)}
+    return {"metric": METRIC, "value": round(spec.cells * 4 * steps / secs / 1e9, 3), "unit": UNIT,
+            "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "switching problem of the time-step study: 480x240x2 cells of 5 nm, Ms 800 kA/m, "
+                                   "S state relaxed, then 1 ns at H = (-20, 1, 0) kA/m", "cells": spec.cells,
+                       "l2": "not flushed (1 ns of dynamics per run)"},
+            "llg_steps_per_s": round(steps / secs, 1), "llg_steps_per_s_extrap": round(xsteps / xsecs, 1),
+            "relax_s": round(relax_s, 2),
+            "eps_vs_25fs_exact": scaling, "mean_m_25fs_exact": samples}
+
+
 def run_reference(args):
     rank, world, local = _dist_env()
     if rank != 0:
@@ -626,7 +725,7 @@ def main():
     ap.add_argument("--llg-steps", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extrap", action="store_true", help="skip the demag-extrapolation run of the film")
-    ap.add_argument("--workload", default="film", choices=["film", "batch", "serve", "3d", "cufft"])
+    ap.add_argument("--workload", default="film", choices=["film", "batch", "serve", "3d", "cufft", "switching"])
     ap.add_argument("--oracle-3d", action="store_true", help="3d: FP64 oracle of the full mesh (minutes, ~30 GB)")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--requests", type=int, default=48)
@@ -644,6 +743,8 @@ def main():
         res = run_3d(args)
     elif args.workload == "cufft":
         res = run_cufft(args)
+    elif args.workload == "switching":
+        res = run_switching(args)
     else:
         res = run_ours(args)
     if res is not None:

@@ -134,6 +134,12 @@ gbd_status gbd_llg_step(gbd_mesh* mesh, float* m, int nsteps, double dt, void* s
 #define GBD_STEP_CONTINUE 2u
 gbd_status gbd_llg_step_ex(gbd_mesh* mesh, float* m, int nsteps, double dt, unsigned flags, void* stream);
 
+/* Changes the applied (Zeeman) field, A/m, and the damping of later calls on the mesh: a
+ * time-dependent field, or relaxation with a larger alpha between dynamics runs. Hext NULL
+ * keeps the field; alpha < 0 keeps the damping. Work already enqueued is unaffected; a batch
+ * re-captures its graph on its next run. GBD_EINVAL for non-finite values. */
+gbd_status gbd_mesh_set_params(gbd_mesh* mesh, const double Hext[3], double alpha);
+
 /* ---- allocation-free demag --------------------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that cannot call
  * cudaMalloc at the moment they need the field -- for example code embedded in a host

@@ -48,6 +48,7 @@ struct gbd_mesh {
   float* hist = nullptr;
   int hist_count = 0, hist_head = 0;
   double hist_dt = 0.0;
+  unsigned version = 0;     // bumped when launch arguments change (params, tuning): batch graphs re-capture
   bool kernel_set = false;
   // optional per-launch timing: events[2i], events[2i+1] bracket launch i of class cls[i]
   bool timing = false;
@@ -401,6 +402,18 @@ gbd_status gbd_mesh_read_timing(gbd_mesh* m, double* ms, long long* launches) {
   }
   m->cls.clear();
   m->used = 0;
+  return GBD_OK;
+}
+
+gbd_status gbd_mesh_set_params(gbd_mesh* m, const double Hext[3], double alpha) {
+  if (!m) return fail(GBD_EINVAL, "mesh is NULL");
+  if (Hext && !(std::isfinite(Hext[0]) && std::isfinite(Hext[1]) && std::isfinite(Hext[2])))
+    return fail(GBD_EINVAL, "Hext must be finite");
+  if (!std::isfinite(alpha)) return fail(GBD_EINVAL, "alpha must be finite (negative keeps the damping)");
+  if (Hext)
+    for (int c = 0; c < 3; ++c) m->d.Hext[c] = Hext[c];
+  if (alpha >= 0) m->d.alpha = alpha;
+  ++m->version;
   return GBD_OK;
 }
 
@@ -845,6 +858,7 @@ void apply_tuning(gbd_mesh* m, const std::array<int, 4>& v) {
   p.Cf = gbd::film_cols(p.Py, p.var_film);
   p.Cy = gbd::ypass_lines(p.Py, p.var_y);
   p.Wz = gbd::zconv_cols(p.Pz, p.var_z);
+  ++m->version;
 }
 
 // Mean device time in ms of one launch made by f(variant), over `reps` launches after one
@@ -998,6 +1012,7 @@ struct gbd_batch {
   std::vector<float*> key_m;
   std::vector<int> key_steps;
   std::vector<double> key_dt;
+  std::vector<unsigned> key_version;
   cudaGraphExec_t exec = nullptr;
 };
 
@@ -1099,9 +1114,11 @@ extern "C" gbd_status gbd_batch_run(gbd_batch* b, float* const* m, const int* ns
   if (s != GBD_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaStream_t og = b->origin;
+  std::vector<unsigned> version(n);
+  for (int i = 0; i < n; ++i) version[i] = b->meshes[i]->version;
   const bool same = b->exec && b->key_m == std::vector<float*>(m, m + n) &&
                     b->key_steps == std::vector<int>(nsteps, nsteps + n) &&
-                    b->key_dt == std::vector<double>(dt, dt + n);
+                    b->key_dt == std::vector<double>(dt, dt + n) && b->key_version == version;
   if (!same) {
     if (b->exec) {
       cudaGraphExecDestroy(b->exec);
@@ -1129,6 +1146,7 @@ extern "C" gbd_status gbd_batch_run(gbd_batch* b, float* const* m, const int* ns
     b->key_m.assign(m, m + n);
     b->key_steps.assign(nsteps, nsteps + n);
     b->key_dt.assign(dt, dt + n);
+    b->key_version = version;
   }
   // order the graph after the caller's earlier work on `stream`, and later work after it
   cudaEventRecord(b->ev_in, st);

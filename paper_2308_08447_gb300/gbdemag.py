@@ -49,6 +49,7 @@ _SIG = {
     "gbd_llg_rhs": [_P, _P, _P, _P],
     "gbd_llg_step": [_P, _P, _I, _D, _P],
     "gbd_llg_step_ex": [_P, _P, _I, _D, ctypes.c_uint, _P],
+    "gbd_mesh_set_params": [_P, ctypes.POINTER(_D), _D],
     "gbd_mesh_destroy": [_P],
     "gbd_tensor_at": [ctypes.POINTER(gbd_mesh_desc), _I, _I, _I, ctypes.POINTER(_D)],
     "gbd_plan_dims": [ctypes.POINTER(gbd_mesh_desc), ctypes.POINTER(_I)],
@@ -197,6 +198,13 @@ def gbd_llg_step_ex(mesh, m, nsteps, dt, flags, shape, stream=None):
                                   _stream_ptr(stream)))
 
 
+def gbd_mesh_set_params(mesh, Hext=None, alpha=None):
+    h = None
+    if Hext is not None:
+        h = (_D * 3)(*(float(v) for v in Hext))
+    _check(load().gbd_mesh_set_params(mesh, h, -1.0 if alpha is None else float(alpha)))
+
+
 def gbd_mesh_destroy(mesh):
     _check(load().gbd_mesh_destroy(mesh))
 
@@ -317,6 +325,10 @@ class Mesh:
         else:
             flags = (GBD_STEP_EXTRAP if extrap else 0) | (GBD_STEP_CONTINUE if cont else 0)
             gbd_llg_step_ex(self.handle, m, nsteps, dt, flags, self.shape, stream)
+
+    def set_params(self, Hext=None, alpha=None):
+        """Applied field (A/m) and/or damping of later calls (None keeps the current value)."""
+        gbd_mesh_set_params(self.handle, Hext, alpha)
 
     def autotune(self, stream=None):
         gbd_mesh_autotune(self.handle, stream)

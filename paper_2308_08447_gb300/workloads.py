@@ -13,6 +13,8 @@ Workloads (the paper measures on synthetic micromagnetic problems only):
   normalised -- the 1024x1024x1 thin film (2x2x3 nm cells).
 * ``batch_meshes`` / ``served_requests``: seeded mesh-size and material
   mixes for the batched and served patterns.
+* ``switching``: the switching problem of the paper's time-step study (Fig. 2),
+  a deterministic start (``uniform``) and a stated relax protocol.
 """
 from dataclasses import dataclass, field
 
@@ -88,6 +90,30 @@ def thin_film():
 def large_3d():
     return MeshSpec(n=(512, 512, 64), cell=(4e-9, 4e-9, 4e-9), Ms=8.0e5, A_ex=1.3e-11,
                     alpha=0.02, dt=1e-13, steps=100, seed=3)
+
+
+def switching(scale=1):
+    """The switching problem of Fig. 2 (Sec. II): a 2.4 um x 1.2 um x 10 nm film in 5 nm cells
+    (480 x 240 x 2), Ms = 800 kA/m, switched by H = (-20, 1, 0) kA/m for 1 ns from an S state.
+
+    Readings where the paper is silent: A = 1.3e-11 J/m and alpha = 0.02 during switching;
+    the S state is prepared from m = [1, 1, 1]/sqrt(3) in a field along [1, 1, 1] stepped from
+    1 MA/m down to 0 in eleven holds (1.0, 0.9, ..., 0.0 MA/m) of 50 ps each at alpha = 0.5.
+    scale > 1 shrinks the film by that factor in x and y (same cells), for parity tests."""
+    nx, ny = 480 // scale, 240 // scale
+    u = 1.0 / np.sqrt(3.0)
+    return MeshSpec(n=(nx, ny, 2), cell=(5e-9, 5e-9, 5e-9), Ms=8.0e5, A_ex=1.3e-11, alpha=0.02, dt=1e-13,
+                    Hext=(-2.0e4, 1.0e3, 0.0), seed=0,
+                    meta={"m_init": (u, u, u), "relax_fields": [1e6 * (1.0 - 0.1 * k) for k in range(11)],
+                          "relax_dir": (u, u, u), "relax_alpha": 0.5, "relax_hold": 50e-12, "t_switch": 1e-9})
+
+
+def uniform(n, direction):
+    """(3, nz, ny, nx) float32: every cell along the unit vector `direction`."""
+    nx, ny, nz = n
+    d = np.asarray(direction, np.float64)
+    d = d / np.linalg.norm(d)
+    return np.broadcast_to(d[:, None, None, None], (3, nz, ny, nx)).astype(np.float32).copy()
 
 
 def stable_dt(cell, Ms, A_ex, gamma=2.212761569e5, mu0=4e-7 * np.pi, cap=1e-13):

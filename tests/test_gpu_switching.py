@@ -1,0 +1,71 @@
+"""The switching workload (Fig. 2, Sec. II) and the mesh-parameter updates it relies on.
+
+Its steps against the oracle on a reduced film of the same cells (96 x 48 x 2 of 5 nm) under
+the switching field; gbd_mesh_set_params must act exactly like creating the mesh with the new
+field and damping, also for a batch captured before the change.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import lib, to_dev, to_host
+from oracle import llg as L
+from oracle import tensor as T
+from paper_2308_08447_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    return lib()
+
+
+def test_switching_steps_track_oracle(g):
+    spec = W.switching(scale=5)
+    m0 = W.uniform(spec.n, spec.meta["m_init"])
+    mesh = g.Mesh(spec.n, spec.cell, spec.Ms, A_ex=spec.A_ex, alpha=spec.alpha, Hext=spec.Hext)
+    md = to_dev(m0)
+    mesh.llg_step(md, 6, 2e-13)
+    got = to_host(md)
+    mesh.close()
+    Nf = T.tensor_all_offsets(spec.n, spec.cell)
+    want = L.llg_run(m0.astype(np.float64), 6, 2e-13, Nf, spec.cell, spec.Ms, spec.A_ex, spec.alpha, Hext=spec.Hext)
+    assert np.abs(got - want).max() < 2e-5
+
+
+def test_set_params_equals_new_mesh(g):
+    n, cell = (64, 32, 2), (5e-9, 5e-9, 5e-9)
+    m0 = W.random_unit(n, 51)
+    H1, H2 = (1e5, 0.0, 0.0), (-2e4, 1e3, 5e2)
+    a = g.Mesh(n, cell, 8e5, A_ex=1.3e-11, alpha=0.5, Hext=H1)
+    b = g.Mesh(n, cell, 8e5, A_ex=1.3e-11, alpha=0.02, Hext=H2)
+    ma, mb = to_dev(m0), to_dev(m0)
+    a.llg_step(ma, 2, 1e-13)
+    a.set_params(Hext=H2, alpha=0.02)
+    ma.copy_(mb)
+    a.llg_step(ma, 3, 1e-13)
+    b.llg_step(mb, 3, 1e-13)
+    assert np.array_equal(to_host(ma), to_host(mb))
+    with pytest.raises(g.GbdError):
+        a.set_params(Hext=(float("nan"), 0.0, 0.0))
+    a.close()
+    b.close()
+
+
+def test_batch_recaptures_after_set_params(g):
+    n, cell = (64, 32, 1), (4e-9, 4e-9, 4e-9)
+    m0 = W.random_unit(n, 52)
+    mesh = g.Mesh(n, cell, 8e5, A_ex=1.3e-11, alpha=0.1, Hext=(0.0, 0.0, 0.0))
+    batch = g.Batch([mesh])
+    mb = to_dev(m0)
+    batch.run([mb], [3], [1e-13])
+    mesh.set_params(Hext=(0.0, 0.0, 2e5))
+    mb.copy_(to_dev(m0))
+    batch.run([mb], [3], [1e-13])
+    ref = g.Mesh(n, cell, 8e5, A_ex=1.3e-11, alpha=0.1, Hext=(0.0, 0.0, 2e5))
+    mr = to_dev(m0)
+    ref.llg_step(mr, 3, 1e-13)
+    assert np.array_equal(to_host(mb), to_host(mr))
+    batch.close()
+    mesh.close()
+    ref.close()
