@@ -501,12 +501,13 @@ static gbd_status upload_spectrum(gbd_mesh* m, const std::vector<double>& spec, 
         for (int c = 0; c < 4; ++c)
           packed[((size_t)kx * p.Ky + ky) * 4 + c] = (float)spec[c * comp + (size_t)ky * p.Hx + kx];
   } else {
-    // [kx][ky][kz] x (xx, yy, zz, xy, xz, yz)
-    for (int kx = 0; kx < p.Hx; ++kx)
-      for (int ky = 0; ky < p.Ky; ++ky)
-        for (int kz = 0; kz < p.Kz; ++kz)
+    // [kz][kx][ky] x (xx, yy, zz, xy, xz, yz): the z convolution's lanes take consecutive
+    // (kx, ky) columns at one kz, so they read consecutive entries
+    for (int kz = 0; kz < p.Kz; ++kz)
+      for (int kx = 0; kx < p.Hx; ++kx)
+        for (int ky = 0; ky < p.Ky; ++ky)
           for (int c = 0; c < 6; ++c)
-            packed[(((size_t)kx * p.Ky + ky) * p.Kz + kz) * 6 + c] =
+            packed[(((size_t)kz * p.Hx + kx) * p.Ky + ky) * 6 + c] =
                 (float)spec[c * comp + (size_t)kz * plane + (size_t)ky * p.Hx + kx];
   }
   cudaError_t e = cudaMemcpyAsync(m->K, packed.data(), p.bytes_K, cudaMemcpyHostToDevice, st);

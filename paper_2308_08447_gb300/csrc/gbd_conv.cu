@@ -2,6 +2,8 @@
 // the transformed tensor (Appendix A, KernelMultiplication) fused with the transforms along
 // the last axis -- y for a single-layer mesh (nz = 1), z for 3D meshes ("pipelined
 // convolution ... in the same routine", Appendix A).
+#include <type_traits>
+
 #include "gbd_launch.cuh"
 
 namespace gbd {
@@ -120,7 +122,8 @@ __global__ void __launch_bounds__(3 * C_ * L / GBD_E, min_blocks_film(3 * C_ * L
 // 3D y passes over independent lines l = (c*nz + z)*Hx + kx: forward S (ny) -> T (Py),
 // inverse T (Py) -> S (first ny).
 template <int L, int W_, int PREC>
-__global__ void __launch_bounds__(3 * W_ * L / GBD_E, min_blocks(3 * W_ * L / GBD_E))
+__global__ void __launch_bounds__(3 * W_ * L / GBD_E,
+                                  PREC == 0 ? min_blocks_film(3 * W_ * L / GBD_E) : min_blocks(3 * W_ * L / GBD_E))
     z_conv_kernel(ColArgs a, const float2* __restrict__ tw) {
   constexpr int W = W_;
   constexpr int LINES = 3 * W;
@@ -130,7 +133,6 @@ __global__ void __launch_bounds__(3 * W_ * L / GBD_E, min_blocks(3 * W_ * L / GB
   constexpr int RL = radix_at(L, true, NP - 1);
   constexpr int NSL = ns_at(L, true, NP - 1);
   constexpr int LR = L / RL;
-  constexpr int KZ = L / 2 + 1;
   extern __shared__ float2 sm[];
   const long long q0 = (long long)blockIdx.x * W;
   const int nz = a.nz;
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(3 * W_ * L / GBD_E, min_blocks(3 * W_ * L / GB
         kyp = Py - ky;
         sy = -1.f;
       }
-      const float* kbase = a.K3 + ((long long)kx * KY + kyp) * KZ * 6;
+      const float* kbase = a.K3 + ((long long)kx * KY + kyp) * 6;   // + kz' Hx KY 6
       auto mul = [&](int kz, float2& m0, float2& m1, float2& m2) {
         if (q >= Q) return;
         int kzp = kz;
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(3 * W_ * L / GBD_E, min_blocks(3 * W_ * L / GB
           kzp = L - kz;
           sz = -1.f;
         }
-        const float* kp = kbase + kzp * 6;
+        const float* kp = kbase + (long long)kzp * a.Hx * KY * 6;
         const float2 k01 = __ldg(reinterpret_cast<const float2*>(kp));
         const float2 k23 = __ldg(reinterpret_cast<const float2*>(kp + 2));
         const float2 k45 = __ldg(reinterpret_cast<const float2*>(kp + 4));
@@ -190,7 +192,53 @@ __global__ void __launch_bounds__(3 * W_ * L / GBD_E, min_blocks(3 * W_ * L / GB
     pass_any<PREC, -1, false, L, radix_at(L, true, 0), 1, LINES, true, false>(tw, gld, sst);
     __syncthreads();
     fwd_passes_smem<-1, L, true, LINES, true, LS, 1, NP - 1, PREC>(sm, tw);
-    run_fused(sld, sst);
+    // The last forward pass, the product and the first adjoint pass as three in-place phases
+    // over all threads: the last pass (Ns R = L) leaves frequency j + q L/R at the position
+    // it read, so each phase touches only its own items' positions.
+    auto last_pass = [&](auto adj) {
+      constexpr bool ADJ = decltype(adj)::value;
+      for (int it = threadIdx.x; it < LINES * LR; it += T) {
+        const int line = it % LINES, j = it / LINES;
+        float2 v[RL];
+#pragma unroll
+        for (int r = 0; r < RL; ++r) v[r] = sld(line, j + r * LR);
+        butterfly<ADJ ? 1 : -1, RL, NSL, ADJ>(v, j, tw);
+#pragma unroll
+        for (int r = 0; r < RL; ++r) sst(line, j + r * LR, v[r]);
+      }
+    };
+    last_pass(std::false_type());
+    __syncthreads();
+    // product at (column w, frequency kz): consecutive lanes take consecutive columns
+    for (int it = threadIdx.x; it < W * L; it += T) {
+      const int w = it % W, kz = it / W;
+      const long long q = q0 + w;
+      if (q >= Q) continue;
+      const int kx = (int)(q / Pyq);
+      const int ky = (int)(q - (long long)kx * Pyq);
+      int kyp = ky, kzp = kz;
+      float sy = 1.f, sz = 1.f;
+      if (Py > 1 && ky > Py / 2) {
+        kyp = Py - ky;
+        sy = -1.f;
+      }
+      if (kz > L / 2) {
+        kzp = L - kz;
+        sz = -1.f;
+      }
+      const float* kp = a.K3 + (((long long)kzp * a.Hx + kx) * KY + kyp) * 6;
+      const float2 k01 = __ldg(reinterpret_cast<const float2*>(kp));
+      const float2 k23 = __ldg(reinterpret_cast<const float2*>(kp + 2));
+      const float2 k45 = __ldg(reinterpret_cast<const float2*>(kp + 4));
+      const float kxx = k01.x, kyy = k01.y, kzz = k23.x;
+      const float kxy = sy * k23.y, kxz = sz * k45.x, kyz = sy * sz * k45.y;
+      const float2 m0 = sld(w, kz), m1 = sld(W + w, kz), m2 = sld(2 * W + w, kz);
+      sst(w, kz, make_float2(kxx * m0.x + kxy * m1.x + kxz * m2.x, kxx * m0.y + kxy * m1.y + kxz * m2.y));
+      sst(W + w, kz, make_float2(kxy * m0.x + kyy * m1.x + kyz * m2.x, kxy * m0.y + kyy * m1.y + kyz * m2.y));
+      sst(2 * W + w, kz, make_float2(kxz * m0.x + kyz * m1.x + kzz * m2.x, kxz * m0.y + kyz * m1.y + kzz * m2.y));
+    }
+    __syncthreads();
+    last_pass(std::true_type());
     __syncthreads();
     adj_passes_smem<1, L, true, LINES, true, LS, NP - 1, 1, PREC>(sm, tw);
     pass_any<PREC, 1, true, L, radix_at(L, true, 0), 1, LINES, true, false>(tw, sld, gst);

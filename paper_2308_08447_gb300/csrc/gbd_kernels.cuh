@@ -83,7 +83,7 @@ struct ColArgs {
   const float2* src;
   float2* dst;
   const float4* Kf;         // film kernel [Hx][Py/2+1] (xx, yy, zz, xy)
-  const float* K3;          // 3D kernel [Hx][Py/2+1][Pz/2+1][6]
+  const float* K3;          // 3D kernel [Pz/2+1][Hx][Py/2+1][6]
   long long Q;              // z-conv columns per plane = Hx * Py (Hx when ny == 1)
   int Pyq;                  // y extent of the column index q (Py, or 1 when ny == 1)
 };

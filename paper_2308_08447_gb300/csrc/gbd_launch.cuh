@@ -8,8 +8,9 @@
 namespace gbd {
 
 __host__ __device__ constexpr int min_blocks(int T) { return T >= 768 ? 1 : 768 / T; }
-// The film convolution runs at 1152 threads per SM (three blocks of 384 at <= 56 registers):
-// its fused pass holds at most two components' values at a time.
+// The FP32 convolution kernels run at 1152 threads per SM (three blocks of 384 at <= 56
+// registers): the film's fused pass holds at most two components' values at a time, and the
+// 3D z convolution splits its fused pass into per-component butterflies and a product phase.
 __host__ __device__ constexpr int min_blocks_film(int T) { return T >= 1152 ? 1 : 1152 / T; }
 
 // Raises the dynamic shared-memory limit of kernel k once per (kernel, device). Meshes call
