@@ -65,12 +65,26 @@ typedef struct {
   double gamma;          /* gyromagnetic ratio mu0*gamma_e, m/(A s); 0 selects 2.212761569e5 */
   double Hext[3];        /* uniform applied (Zeeman) field, A/m */
   int precision;         /* gbd_precision */
-  unsigned flags;        /* reserved, 0 */
+  unsigned flags;        /* GBD_FLAG_PBC_* bits (0: open boundaries everywhere) */
+  int pbc_images;        /* periodic images per side along each periodic axis (>= 1 with one) */
 } gbd_mesh_desc;
+
+/* Periodic boundary conditions (Sec. II: a modified kernel and no zero padding along the
+ * periodic direction). Along a periodic axis d the magnetization repeats with period n_d, which
+ * must be a power of two (n_x >= 2 for x): the convolution along d is circular of length n_d, the
+ * kernel is the demag tensor summed over pbc_images images on each side (at the half-period
+ * offset the +n_d/2 and -n_d/2 image sets are averaged, so every component keeps its parity),
+ * and the exchange Laplacian wraps around. Images beyond 256 cell sizes enter as point dipoles.
+ * The kernel set-up costs about octant * (2 pbc_images + 1)^(periodic axes) tensor terms on
+ * the host. gbd_set_kernel_tensor is not available for periodic meshes (GBD_EUNSUPPORTED). */
+#define GBD_FLAG_PBC_X 1u
+#define GBD_FLAG_PBC_Y 2u
+#define GBD_FLAG_PBC_Z 4u
 
 typedef struct gbd_mesh gbd_mesh; /* opaque: plan, kernel spectrum, scratch, RK4 state */
 
-/* Validates desc, plans the padded lengths (powers of two >= 2n - 1; 1 where n = 1) and
+/* Validates desc, plans the padded lengths (powers of two >= 2n - 1; 1 where n = 1; n along a
+ * periodic axis) and
  * allocates the mesh's device buffers on the current device: x spectrum, 3D y spectrum,
  * kernel spectrum, RK4 scratch, twiddle table. *out receives the mesh (NULL on failure).
  * Errors: GBD_EINVAL, GBD_EUNSUPPORTED, GBD_ENOMEM, GBD_ECUDA. */

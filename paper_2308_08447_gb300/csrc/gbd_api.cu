@@ -90,18 +90,33 @@ static int pow2_at_least(long long v) {
   return p;
 }
 
-bool make_plan(int nx, int ny, int nz, Plan& p, const char** why) {
+bool make_plan(int nx, int ny, int nz, int per, Plan& p, const char** why) {
   if (nx < 1 || ny < 1 || nz < 1) {
     *why = "mesh sizes must be >= 1";
+    return false;
+  }
+  const int n[3] = {nx, ny, nz};
+  for (int d = 0; d < 3; ++d)
+    if ((per >> d & 1) && (n[d] & (n[d] - 1)) != 0) {
+      *why = "a periodic axis needs a power-of-two number of cells";
+      return false;
+    }
+  if ((per & 1) && nx < 2) {
+    *why = "a periodic x axis needs nx >= 2";
     return false;
   }
   p.nx = nx;
   p.ny = ny;
   p.nz = nz;
   p.N = (long long)nx * ny * nz;
-  p.Px = nx == 1 ? 2 : pow2_at_least(2LL * nx - 1);
-  p.Py = ny == 1 ? 1 : pow2_at_least(2LL * ny - 1);
-  p.Pz = nz == 1 ? 1 : pow2_at_least(2LL * nz - 1);
+  p.per = per;
+  // periodic: the period itself (circular convolution); otherwise zero padded
+  p.Px = (per & 1) ? nx : (nx == 1 ? 2 : pow2_at_least(2LL * nx - 1));
+  p.Py = (per & 2) ? ny : (ny == 1 ? 1 : pow2_at_least(2LL * ny - 1));
+  p.Pz = (per & 4) ? nz : (nz == 1 ? 1 : pow2_at_least(2LL * nz - 1));
+  p.ox = (per & 1) ? nx / 2 + 1 : nx;
+  p.oy = (per & 2) ? ny / 2 + 1 : ny;
+  p.oz = (per & 4) ? nz / 2 + 1 : nz;
   if (p.Px > kMaxPadX || p.Py > kMaxPad || p.Pz > kMaxPad) {
     *why = "mesh too large: supported nx <= 4096, ny <= 2048, nz <= 2048";
     return false;
@@ -126,6 +141,8 @@ bool make_plan(int nx, int ny, int nz, Plan& p, const char** why) {
 
 }  // namespace gbd
 
+constexpr int kMaxImages = 10000;
+
 static gbd_status check_desc(const gbd_mesh_desc* d, gbd::Plan& p) {
   if (!d) return fail(GBD_EINVAL, "desc is NULL");
   const char* why = nullptr;
@@ -140,7 +157,13 @@ static gbd_status check_desc(const gbd_mesh_desc* d, gbd::Plan& p) {
     if (!std::isfinite(d->Hext[i])) return fail(GBD_EINVAL, "Hext must be finite");
   if (d->precision != GBD_FP32 && d->precision != GBD_SPLIT_BF16)
     return fail(GBD_EUNSUPPORTED, "precision must be GBD_FP32 or GBD_SPLIT_BF16");
-  if (!gbd::make_plan(d->nx, d->ny, d->nz, p, &why)) return fail(GBD_EUNSUPPORTED, why);
+  if (d->flags & ~(unsigned)(GBD_FLAG_PBC_X | GBD_FLAG_PBC_Y | GBD_FLAG_PBC_Z))
+    return fail(GBD_EINVAL, "unknown flags");
+  const int per = (int)(d->flags & 7u);
+  if (per && (d->pbc_images < 1 || d->pbc_images > kMaxImages))
+    return fail(GBD_EINVAL, "pbc_images must be in [1, " + std::to_string(kMaxImages) + "] with a periodic axis");
+  if (!gbd::make_plan(d->nx, d->ny, d->nz, per, p, &why)) return fail(GBD_EUNSUPPORTED, why);
+  p.images = per ? d->pbc_images : 0;
   p.prec = (d->precision == GBD_SPLIT_BF16) ? 1 : 0;
   return GBD_OK;
 }
@@ -198,6 +221,7 @@ static gbd::RowArgs row_args(const gbd_mesh* m) {
   a.geff = (float)(gam / (1.0 + d.alpha * d.alpha));
   a.alpha = (float)d.alpha;
   a.hscale = (float)d.Ms;
+  a.per = p.per;
   return a;
 }
 
@@ -433,13 +457,16 @@ namespace {
 struct GeoKey {
   int nx, ny, nz;
   double dx, dy, dz;
+  int per, images;   // periodic axes and images per side
   bool operator<(const GeoKey& o) const {
     if (nx != o.nx) return nx < o.nx;
     if (ny != o.ny) return ny < o.ny;
     if (nz != o.nz) return nz < o.nz;
     if (dx != o.dx) return dx < o.dx;
     if (dy != o.dy) return dy < o.dy;
-    return dz < o.dz;
+    if (dz != o.dz) return dz < o.dz;
+    if (per != o.per) return per < o.per;
+    return images < o.images;
   }
 };
 struct SpecEntry {
@@ -523,7 +550,7 @@ gbd_status gbd_set_kernel(gbd_mesh* m, void* stream) {
   gbd_status s = check_device(m);
   if (s != GBD_OK) return s;
   const gbd::Plan& p = m->p;
-  const GeoKey key{p.nx, p.ny, p.nz, m->d.dx, m->d.dy, m->d.dz};
+  const GeoKey key{p.nx, p.ny, p.nz, m->d.dx, m->d.dy, m->d.dz, p.per, p.images};
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (auto hit = spec_cache_get(key)) {
     cudaError_t e = cudaMemcpyAsync(m->K, hit->data(), p.bytes_K, cudaMemcpyHostToDevice, st);
@@ -540,6 +567,7 @@ gbd_status gbd_set_kernel(gbd_mesh* m, void* stream) {
 // Spectrum of a caller tensor [6][2nz-1][2ny-1][2nx-1] (see gbd_set_kernel_tensor).
 static gbd_status spectrum_of_tensor(const gbd::Plan& p, const double* N6, std::vector<double>& spec) {
   if (!N6) return fail(GBD_EINVAL, "tensor is NULL");
+  if (p.per) return fail(GBD_EUNSUPPORTED, "caller tensors are not available for periodic meshes");
   std::vector<double> oct;
   const int r = gbdt::octant_from_full(p, N6, oct, GBD_TENSOR_SYM_TOL);
   if (r < 0) return fail(GBD_ENOMEM, "host allocation failed");

@@ -68,6 +68,8 @@ struct RowArgs {
   float geff, alpha;        // gamma / (1 + alpha^2), alpha
   float dt;                 // time step, s
   int vec8;                 // the field pointers allow 8-byte accesses (set by launch_row)
+  int per;                  // periodic axes (bit 0 x, 1 y, 2 z): the x transform has no zero
+                            // half, and the exchange Laplacian wraps around
   // demag extrapolation at RK4 sub-steps (Sec. III): with extrap the stage's demag field is
   // sum_k hw[k] hist[k] over the step-start history (newest first) and no inverse transform
   // runs; hrec, when set, receives the stage's demag field (hscale * H_d), [3][N]

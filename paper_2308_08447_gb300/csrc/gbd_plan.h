@@ -20,6 +20,10 @@ struct Plan {
   int Lx = 0, Hx = 0;   // Lx = Px / 2, Hx = Lx + 1 stored x frequencies
   int Ky = 0, Kz = 0;   // stored y / z kernel frequencies: P/2 + 1 (1 when P = 1)
   bool film = false;    // nz == 1: 3-pass path
+  // periodic axes (bit 0 x, 1 y, 2 z): P_d = n_d, no padding, kernel summed over `images`
+  // periodic images per side; the kernel octant then spans n_d/2 + 1 offsets along d
+  int per = 0, images = 0;
+  int ox = 0, oy = 0, oz = 0;   // kernel octant extents (n_d when not periodic)
   // tile variants (0 / 1) per kernel family, set by the autotuner, and the block shapes
   // they give
   int var_row = 1, var_film = 0, var_y = 0, var_z = 0;
@@ -34,8 +38,9 @@ struct Plan {
   size_t total_bytes() const { return bytes_S + bytes_T + bytes_K + bytes_state + bytes_tw; }
 };
 
-// Fills p from the mesh size; returns false (with a message) when the mesh is out of range.
-bool make_plan(int nx, int ny, int nz, Plan& p, const char** why);
+// Fills p from the mesh size and periodic axes; returns false (with a message) when the mesh
+// is out of range.
+bool make_plan(int nx, int ny, int nz, int per, Plan& p, const char** why);
 
 }  // namespace gbd
 

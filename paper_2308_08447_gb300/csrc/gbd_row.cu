@@ -124,22 +124,31 @@ __device__ __forceinline__ bool epilogue_pair(const RowArgs& a, int mode, int z,
     for (int c = 0; c < 3; ++c) *reinterpret_cast<float2*>(a.out + c * N + idx) = make_float2(hd[0][c], hd[1][c]);
     return false;
   }
+  // neighbour offsets, once per pair: the adjacent cell, across a periodic axis the cell on the
+  // opposite face, else (free boundary) the cell itself
+  const long long wy = (long long)(ny - 1) * nx, wz = (long long)(a.nz - 1) * sz;
+  const long long oym = y > 0 ? -(long long)nx : ((a.per & 2) ? wy : 0);
+  const long long oyp = y < ny - 1 ? (long long)nx : ((a.per & 2) ? -wy : 0);
+  const long long ozm = z > 0 ? -sz : ((a.per & 4) ? wz : 0);
+  const long long ozp = z < a.nz - 1 ? sz : ((a.per & 4) ? -wz : 0);
+  const int oxl = x0 > 0 ? -1 : ((a.per & 1) ? nx - 1 : 0);      // left of x0 (lane 0)
+  const int oxr = x0 + 2 < nx ? 2 : ((a.per & 1) ? 2 - nx : 1);  // right of x0 + 1 (lane 31)
   float mv[2][3], lap[2][3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const float* __restrict__ p = a.ms + c * N + idx;
     const float2 cc = *reinterpret_cast<const float2*>(p);
-    const float2 ym = y > 0 ? *reinterpret_cast<const float2*>(p - nx) : cc;
-    const float2 yp = y < ny - 1 ? *reinterpret_cast<const float2*>(p + nx) : cc;
+    const float2 ym = *reinterpret_cast<const float2*>(p + oym);
+    const float2 yp = *reinterpret_cast<const float2*>(p + oyp);
     float2 zm = cc, zp = cc;
     if (a.nz > 1) {
-      if (z > 0) zm = *reinterpret_cast<const float2*>(p - sz);
-      if (z < a.nz - 1) zp = *reinterpret_cast<const float2*>(p + sz);
+      zm = *reinterpret_cast<const float2*>(p + ozm);
+      zp = *reinterpret_cast<const float2*>(p + ozp);
     }
     float left = __shfl_up_sync(0xffffffffu, cc.y, 1);
     float right = __shfl_down_sync(0xffffffffu, cc.x, 1);
-    if (lane == 0) left = x0 > 0 ? p[-1] : cc.x;
-    if (lane == 31) right = x0 + 2 < nx ? p[2] : cc.y;
+    if (lane == 0) left = p[oxl];
+    if (lane == 31) right = p[oxr];
     mv[0][c] = cc.x;
     mv[1][c] = cc.y;
     lap[0][c] = a.cx * (left - 2.f * cc.x + cc.y) + a.cy * (ym.x - 2.f * cc.x + yp.x) + a.cz * (zm.x - 2.f * cc.x + zp.x);
@@ -194,10 +203,15 @@ __device__ __forceinline__ bool epilogue_cell(const RowArgs& a, int mode, int z,
     for (int c = 0; c < 3; ++c) a.out[c * N + idx] = hd[c];
     return false;
   }
-  // exchange: 7-point Laplacian, free boundaries (missing neighbour = the cell itself)
-  const long long ixm = x > 0 ? idx - 1 : idx, ixp = x < nx - 1 ? idx + 1 : idx;
-  const long long iym = y > 0 ? idx - nx : idx, iyp = y < ny - 1 ? idx + nx : idx;
-  const long long izm = z > 0 ? idx - sz : idx, izp = z < a.nz - 1 ? idx + sz : idx;
+  // exchange: 7-point Laplacian; a missing neighbour is the cell itself (free boundary) or,
+  // across a periodic axis, the cell on the opposite face
+  const bool px = a.per & 1, py = a.per & 2, pz = a.per & 4;
+  const long long ixm = x > 0 ? idx - 1 : (px ? idx + (nx - 1) : idx);
+  const long long ixp = x < nx - 1 ? idx + 1 : (px ? idx - (nx - 1) : idx);
+  const long long iym = y > 0 ? idx - nx : (py ? idx + (long long)(ny - 1) * nx : idx);
+  const long long iyp = y < ny - 1 ? idx + nx : (py ? idx - (long long)(ny - 1) * nx : idx);
+  const long long izm = z > 0 ? idx - sz : (pz ? idx + (long long)(a.nz - 1) * sz : idx);
+  const long long izp = z < a.nz - 1 ? idx + sz : (pz ? idx - (long long)(a.nz - 1) * sz : idx);
   float mv[3], lap[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -273,6 +287,9 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
   constexpr int HX = LX + 1;
   constexpr int HALF = LX / 2;
   constexpr int FL = NP >= 1 ? LX : 2 * LX;    // real samples the forward transform reads
+  // periodic x (Px = nx, no zero padding): the whole line holds data
+  const bool xper = (a.per & 1) != 0;
+  const int flr = xper ? 2 * LX : FL;          // real samples of a line that hold data or zeros
   extern __shared__ float2 sm[];
   const int r0 = blockIdx.x * RB;
   const long long N = a.N;
@@ -368,10 +385,15 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
     if constexpr (NP >= 1) {
       adj_passes_smem<1, LX, false, LINES, false, LS, NP, 1, PREC>(sm, tw);
       auto ld = [&](int line, int i) { return sm[line * LS + pad(i)]; };
-      auto st = [&](int line, int i, float2 v) {
+      // the bound is a compile-time constant on the open-boundary path, so the pass is pruned
+      auto st_half = [&](int line, int i, float2 v) {
         if (i < HALF) sm[line * LS + pad(i)] = v;
       };
-      pass_any<PREC, 1, true, LX, radix_at(LX, false, 0), 1, LINES, false, true>(tw, ld, st);
+      auto st_all = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
+      if (xper)
+        pass_any<PREC, 1, true, LX, radix_at(LX, false, 0), 1, LINES, false, true>(tw, ld, st_all);
+      else
+        pass_any<PREC, 1, true, LX, radix_at(LX, false, 0), 1, LINES, false, true>(tw, ld, st_half);
       __syncthreads();
     }
     }
@@ -434,35 +456,37 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
       const int rr = line % RB;
       const int x0 = (r0 + rr < a.rows) ? nx : 0;
       float* fl = reinterpret_cast<float*>(sm + line * LS);
-      for (int x = x0 + threadIdx.x; x < FL; x += T) fl[2 * pad(x >> 1) + (x & 1)] = 0.f;
+      for (int x = x0 + threadIdx.x; x < flr; x += T) fl[2 * pad(x >> 1) + (x & 1)] = 0.f;
     }
   } else {
     // forward only: the input rows into the float view, zero beyond nx; pairs of samples
     // are one complex slot, read as 8-byte vectors when nx is even
-    constexpr int PAIRS = LINES * (FL / 2);
-    constexpr int IPT = (PAIRS + T - 1) / T;
-    if (FL >= 2 && (nx % 2) == 0 && a.vec8) {
+    constexpr int PAIRS_MAX = LINES * LX;   // a whole line (periodic x)
+    constexpr int IPT = (PAIRS_MAX + T - 1) / T;
+    const int hl = flr / 2;                 // complex slots per line to fill
+    const int pairs = LINES * hl;
+    if (flr >= 2 && (nx % 2) == 0 && a.vec8) {
       float2 v[IPT];
 #pragma unroll
       for (int i = 0; i < IPT; ++i) {
         const int e = threadIdx.x + i * T;
-        const int line = e / (FL / 2);
-        const int xp = e % (FL / 2);
+        const int line = e / hl;
+        const int xp = e % hl;
         const int c = line / RB, rr = line % RB;
         v[i] = make_float2(0.f, 0.f);
-        if (e < PAIRS && 2 * xp < nx && r0 + rr < a.rows)
+        if (e < pairs && 2 * xp < nx && r0 + rr < a.rows)
           v[i] = *reinterpret_cast<const float2*>(a.in + c * N + (long long)(r0 + rr) * nx + 2 * xp);
       }
 #pragma unroll
       for (int i = 0; i < IPT; ++i) {
         const int e = threadIdx.x + i * T;
-        if (PAIRS % T != 0 && e >= PAIRS) break;
-        sm[(e / (FL / 2)) * LS + pad(e % (FL / 2))] = v[i];
+        if (e >= pairs) break;
+        sm[(e / hl) * LS + pad(e % hl)] = v[i];
       }
     } else {
-      for (int e = threadIdx.x; e < LINES * FL; e += T) {
-        const int line = e / FL;
-        const int x = e % FL;
+      for (int e = threadIdx.x; e < LINES * flr; e += T) {
+        const int line = e / flr;
+        const int x = e % flr;
         const int c = line / RB, rr = line % RB;
         const int row = r0 + rr;
         float v = 0.f;
@@ -474,9 +498,13 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
   __syncthreads();
   // 5. forward FFT; the first pass reads the lower half only (the upper half is zero).
   if constexpr (NP >= 1) {
-    auto ld = [&](int line, int i) { return i < HALF ? sm[line * LS + pad(i)] : make_float2(0.f, 0.f); };
+    auto ld_half = [&](int line, int i) { return i < HALF ? sm[line * LS + pad(i)] : make_float2(0.f, 0.f); };
+    auto ld_all = [&](int line, int i) { return sm[line * LS + pad(i)]; };
     auto st = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
-    pass_any<PREC, -1, false, LX, radix_at(LX, false, 0), 1, LINES, false, true>(tw, ld, st);
+    if (xper)
+      pass_any<PREC, -1, false, LX, radix_at(LX, false, 0), 1, LINES, false, true>(tw, ld_all, st);
+    else
+      pass_any<PREC, -1, false, LX, radix_at(LX, false, 0), 1, LINES, false, true>(tw, ld_half, st);
     __syncthreads();
     fwd_passes_smem<-1, LX, false, LINES, false, LS, 1, NP, PREC>(sm, tw);
   }

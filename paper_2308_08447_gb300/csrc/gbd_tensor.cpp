@@ -27,6 +27,7 @@
 #include <complex>
 #include <cstdlib>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "gbd_plan.h"
@@ -218,21 +219,94 @@ static const int PARITY[6][3] = {{1, 1, 1}, {1, 1, 1}, {1, 1, 1}, {-1, -1, 1}, {
 
 // Packed spectrum, FP64, layout [6][Kz][Ky][Hx] with Hx = Px/2+1, Ky = Py/2+1 (1 if Py = 1),
 // Kz likewise. Returns false on allocation failure.
+// Point-dipole tensor V/(4 pi) (I/r^3 - 3 R R^T / r^5) at offset (X, Y, Z) cells: the far-field
+// limit of the cell-pair average, used for periodic images beyond kImageDipoleR cell sizes.
+static void point_dipole(double X, double Y, double Z, double dx, double dy, double dz, double out[6]) {
+  const double x = X * dx, y = Y * dy, z = Z * dz;
+  const double r2 = x * x + y * y + z * z;
+  const double r = std::sqrt(r2);
+  const double c = dx * dy * dz / (4.0 * PI * r2 * r);
+  const double q = 3.0 / r2;
+  out[0] = c * (1.0 - q * x * x);
+  out[1] = c * (1.0 - q * y * y);
+  out[2] = c * (1.0 - q * z * z);
+  out[3] = -c * q * x * y;
+  out[4] = -c * q * x * z;
+  out[5] = -c * q * y * z;
+}
+
+constexpr double kImageDipoleR = 256.0;   // in units of the largest cell side
+
+// The tensor at a signed offset from its octant value and the component parities.
+static void signed_term(int X, int Y, int Z, double dx, double dy, double dz, double dmax, double out[6]) {
+  const double r = std::sqrt((double)X * X * dx * dx + (double)Y * Y * dy * dy + (double)Z * Z * dz * dz) / dmax;
+  double v[6];
+  if (r >= kImageDipoleR)
+    point_dipole(std::abs(X), std::abs(Y), std::abs(Z), dx, dy, dz, v);
+  else
+    tensor_at(std::abs(X), std::abs(Y), std::abs(Z), dx, dy, dz, v);
+  for (int c = 0; c < 6; ++c) {
+    double s = 1.0;
+    if (X < 0 && PARITY[c][0] < 0) s = -s;
+    if (Y < 0 && PARITY[c][1] < 0) s = -s;
+    if (Z < 0 && PARITY[c][2] < 0) s = -s;
+    out[c] = s * v[c];
+  }
+}
+
+// (offset, weight) terms summed at octant index b of one axis: the offset itself, or along a
+// periodic axis of period n its images b + i n, |i| <= K, with the +n/2 and -n/2 image sets
+// averaged at b = n/2 so that odd components cancel there exactly.
+static void axis_terms(int b, int n, bool periodic, int K, std::vector<std::pair<int, double>>& t) {
+  t.clear();
+  if (!periodic) {
+    t.emplace_back(b, 1.0);
+    return;
+  }
+  for (int i = -K; i <= K; ++i) {
+    if (2 * b == n) {
+      t.emplace_back(b + i * n, 0.5);
+      t.emplace_back(-b + i * n, 0.5);
+    } else {
+      t.emplace_back(b + i * n, 1.0);
+    }
+  }
+}
+
 bool kernel_spectrum(const gbd::Plan& p, double dx, double dy, double dz, std::vector<double>& out) {
-  const int nx = p.nx, ny = p.ny, nz = p.nz;
-  const long long Noct = (long long)nx * ny * nz;
+  const int ox = p.ox, oy = p.oy, oz = p.oz;
+  const long long Noct = (long long)ox * oy * oz;
   std::vector<double> oct;
   try {
     oct.resize((size_t)Noct * 6);
   } catch (...) {
     return false;
   }
-#pragma omp parallel for schedule(dynamic, 64)
-  for (long long i = 0; i < Noct; ++i) {
-    const int X = (int)(i % nx), Y = (int)((i / nx) % ny), Z = (int)(i / ((long long)nx * ny));
-    double v[6];
-    tensor_at(X, Y, Z, dx, dy, dz, v);
-    for (int c = 0; c < 6; ++c) oct[(size_t)c * Noct + i] = v[c];
+  const double dmax = std::fmax(dx, std::fmax(dy, dz));
+#pragma omp parallel
+  {
+    std::vector<std::pair<int, double>> tx, ty, tz;
+#pragma omp for schedule(dynamic, 16)
+    for (long long i = 0; i < Noct; ++i) {
+      const int X = (int)(i % ox), Y = (int)((i / ox) % oy), Z = (int)(i / ((long long)ox * oy));
+      double v[6] = {0, 0, 0, 0, 0, 0};
+      if (p.per == 0) {
+        tensor_at(X, Y, Z, dx, dy, dz, v);
+      } else {
+        axis_terms(X, p.nx, p.per & 1, p.images, tx);
+        axis_terms(Y, p.ny, p.per & 2, p.images, ty);
+        axis_terms(Z, p.nz, p.per & 4, p.images, tz);
+        for (const auto& a : tz)
+          for (const auto& b : ty)
+            for (const auto& e : tx) {
+              double t[6];
+              signed_term(e.first, b.first, a.first, dx, dy, dz, dmax, t);
+              const double w = e.second * b.second * a.second;
+              for (int c = 0; c < 6; ++c) v[c] += w * t[c];
+            }
+      }
+      for (int c = 0; c < 6; ++c) oct[(size_t)c * Noct + i] = v[c];
+    }
   }
   return spectrum_from_octant(p, oct, out);
 }
@@ -280,7 +354,8 @@ int octant_from_full(const gbd::Plan& p, const double* full, std::vector<double>
 }
 
 bool spectrum_from_octant(const gbd::Plan& p, const std::vector<double>& oct, std::vector<double>& out) {
-  const int nx = p.nx, ny = p.ny, nz = p.nz;
+  // octant extents: n_d, or n_d / 2 + 1 along a periodic axis
+  const int nx = p.ox, ny = p.oy, nz = p.oz;
   const long long Noct = (long long)nx * ny * nz;
   try {
     out.assign((size_t)6 * p.Kz * p.Ky * p.Hx, 0.0);

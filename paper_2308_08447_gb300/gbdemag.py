@@ -32,7 +32,7 @@ class gbd_mesh_desc(ctypes.Structure):
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
                 ("Ms", ctypes.c_double), ("A_ex", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("Hext", ctypes.c_double * 3),
-                ("precision", ctypes.c_int), ("flags", ctypes.c_uint)]
+                ("precision", ctypes.c_int), ("flags", ctypes.c_uint), ("pbc_images", ctypes.c_int)]
 
 
 _lib = None
@@ -101,14 +101,19 @@ def _check(status):
         raise GbdError(status, load().gbd_last_error().decode())
 
 
-def make_desc(n, cell, Ms, A_ex=0.0, alpha=0.0, gamma=0.0, Hext=(0.0, 0.0, 0.0), precision=GBD_FP32):
+GBD_FLAG_PBC_X, GBD_FLAG_PBC_Y, GBD_FLAG_PBC_Z = 1, 2, 4
+
+
+def make_desc(n, cell, Ms, A_ex=0.0, alpha=0.0, gamma=0.0, Hext=(0.0, 0.0, 0.0), precision=GBD_FP32, pbc=(False,) * 3,
+              pbc_images=0):
     d = gbd_mesh_desc()
     d.nx, d.ny, d.nz = (int(v) for v in n)
     d.dx, d.dy, d.dz = (float(v) for v in cell)
     d.Ms, d.A_ex, d.alpha, d.gamma = float(Ms), float(A_ex), float(alpha), float(gamma)
     d.Hext[0], d.Hext[1], d.Hext[2] = (float(v) for v in Hext)
     d.precision = int(precision)
-    d.flags = 0
+    d.flags = (GBD_FLAG_PBC_X if pbc[0] else 0) | (GBD_FLAG_PBC_Y if pbc[1] else 0) | (GBD_FLAG_PBC_Z if pbc[2] else 0)
+    d.pbc_images = int(pbc_images)
     return d
 
 
@@ -296,10 +301,10 @@ class Mesh:
     """One mesh: owns the library handle; the kernel spectrum is computed on construction."""
 
     def __init__(self, n, cell, Ms, A_ex=0.0, alpha=0.0, gamma=0.0, Hext=(0.0, 0.0, 0.0),
-                 precision=GBD_FP32, set_kernel=True, stream=None):
+                 precision=GBD_FP32, set_kernel=True, stream=None, pbc=(False,) * 3, pbc_images=0):
         self.n = tuple(int(v) for v in n)
         self.shape = (3, self.n[2], self.n[1], self.n[0])
-        self.desc = make_desc(n, cell, Ms, A_ex, alpha, gamma, Hext, precision)
+        self.desc = make_desc(n, cell, Ms, A_ex, alpha, gamma, Hext, precision, pbc, pbc_images)
         self.handle = gbd_mesh_create(self.desc)
         if set_kernel:
             gbd_set_kernel(self.handle, stream)

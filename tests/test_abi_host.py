@@ -191,3 +191,48 @@ def test_caller_tensor_checks(g):
         g.gbd_kernel_spectrum_from_tensor_host(desc, bad)
     with pytest.raises(ValueError):
         g.gbd_kernel_spectrum_from_tensor_host(desc, N6[:, :, :, :-1])
+
+
+# ---- periodic boundary conditions ----------------------------------------------------------
+
+@pytest.mark.parametrize("n,pbc,images", [((16, 8, 1), (True, True, False), 3), ((16, 12, 4), (True, False, False), 2),
+                                          ((8, 8, 4), (False, False, True), 2), ((4, 8, 2), (True, True, True), 1)])
+def test_periodic_spectrum_matches_oracle(g, n, pbc, images):
+    from oracle import pbc as B
+    cell = (2e-9, 3e-9, 2.5e-9)
+    desc = g.make_desc(n, cell, 8e5, pbc=pbc, pbc_images=images)
+    Px, Py, Pz, Hx, Ky, Kz = g.gbd_plan_dims(desc)
+    assert (Px, Py, Pz) == tuple(n[d] if pbc[d] else (1 if n[d] == 1 and d > 0 else max(2, 1 << (2 * n[d] - 2).bit_length()))
+                                 for d in range(3))
+    spec = g.gbd_kernel_spectrum_host(desc)
+    Kg = B.periodic_kernel(n, cell, pbc, images)
+    P = (Px, Py, Pz)
+    Kp = np.zeros((6, Pz, Py, Px))
+    idx = [np.arange(Kg.shape[3 - d]) if pbc[d] else (np.arange(Kg.shape[3 - d]) - (n[d] - 1)) % P[d] for d in range(3)]
+    for c in range(6):
+        Kp[c][np.ix_(idx[2], idx[1], idx[0])] = Kg[c]
+    Kh = np.fft.fftn(Kp, axes=(1, 2, 3))
+    assert np.abs(Kh.imag).max() <= 1e-10 * np.abs(Kh).max()
+    want = -Kh.real[:, :Kz, :Ky, :Hx] / (Px * Py * Pz)
+    if n[2] == 1:
+        want[4:] = 0.0
+    assert np.abs(spec - want).max() <= 1e-8 * np.abs(want).max()
+
+
+def test_periodic_desc_checks(g):
+    cell = (2e-9, 2e-9, 2e-9)
+    with pytest.raises(g.GbdError) as ei:          # a periodic axis needs a power of two
+        g.gbd_plan_dims(g.make_desc((12, 8, 1), cell, 8e5, pbc=(True, False, False), pbc_images=2))
+    assert ei.value.status == g.GBD_EUNSUPPORTED
+    with pytest.raises(g.GbdError) as ei:          # images >= 1 with a periodic axis
+        g.gbd_plan_dims(g.make_desc((16, 8, 1), cell, 8e5, pbc=(True, False, False), pbc_images=0))
+    assert ei.value.status == g.GBD_EINVAL
+    d = g.make_desc((16, 8, 1), cell, 8e5)
+    d.flags = 64
+    with pytest.raises(g.GbdError) as ei:
+        g.gbd_plan_dims(d)
+    assert ei.value.status == g.GBD_EINVAL
+    with pytest.raises(g.GbdError) as ei:          # caller tensors are for open boundaries
+        g.gbd_kernel_spectrum_from_tensor_host(g.make_desc((4, 4, 1), cell, 8e5, pbc=(True, True, False),
+                                                           pbc_images=1), np.zeros((6, 1, 7, 7)))
+    assert ei.value.status == g.GBD_EUNSUPPORTED
