@@ -434,7 +434,7 @@ def run_serve(args):
 
     torch.cuda.set_device(0)
     os.environ.setdefault("GBD_KERNEL_CACHE_BYTES", str(64 << 30))
-    ex = serve.GpuExecutor()
+    ex = serve.GpuExecutor(extrap=args.extrap)
     jobs = serve.make_jobs(args.requests, args.rate, seed=5)
     t0 = time.perf_counter()
     ex.prewarm(jobs)
@@ -448,13 +448,14 @@ def run_serve(args):
     clocks = sampler.stop()
     by_id = {j.id: j for j in plain}
     identical = all(np.array_equal(j.result, by_id[j.id].result) for j in served)
-    s_served, s_plain = serve.summarize(served), serve.summarize(plain)
+    s_served, s_plain = serve.summarize(served, args.extrap), serve.summarize(plain, args.extrap)
     return {"metric": METRIC, "value": round(s_served["gcell_demag_per_s"], 3), "unit": UNIT, "n_gpus": 1,
             "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "served: %d Poisson-arrival jobs at %.0f/s, continuous batching, %d-step chunks, "
                                    "150 GB budget" % (len(jobs), args.rate, args.chunk),
-                       "max_active_cap": args.max_active or None, "setup_s": round(setup_s, 1)},
+                       "max_active_cap": args.max_active or None, "setup_s": round(setup_s, 1),
+                       "demag_extrapolation": bool(args.extrap)},
             "served": s_served, "plain_path": s_plain, "results_bit_identical": bool(identical),
             "max_active": max(a for _, a, _ in srv.trace), "iterations": len(srv.trace), "clocks": clocks}
 
@@ -732,6 +733,8 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--chunk", type=int, default=50)
     ap.add_argument("--max-active", type=int, default=8, help="served jobs per iteration (0: no cap)")
+    ap.add_argument("--extrap", action="store_true",
+                    help="serve: demag extrapolated at RK4 sub-steps on the served and the plain path")
     args = ap.parse_args()
     if args.impl == "reference":
         res = run_reference(args)

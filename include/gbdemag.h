@@ -218,6 +218,15 @@ gbd_status gbd_batch_create(gbd_mesh* const* meshes, int count, gbd_batch** out)
  * Errors: GBD_EINVAL (NULL / misaligned pointer, nsteps < 0, dt <= 0), GBD_ECUDA. */
 gbd_status gbd_batch_run(gbd_batch* batch, float* const* m, const int* nsteps, const double* dt, void* stream);
 
+/* gbd_batch_run with per-mesh gbd_llg_step_ex flags (NULL: all 0). With GBD_STEP_EXTRAP a
+ * mesh's history advances as in gbd_llg_step_ex; the cached graph is reused while every mesh's
+ * arguments, flags and history state (ring position, fill, dt) repeat, which for a continued
+ * run (GBD_STEP_CONTINUE) holds once the history is full and nsteps is a multiple of 5 (the
+ * ring's length); otherwise the run is captured again. Each mesh's result is bit-identical to
+ * gbd_llg_step_ex on that mesh alone with the same flags. */
+gbd_status gbd_batch_run_ex(gbd_batch* batch, float* const* m, const int* nsteps, const double* dt,
+                            const unsigned* flags, void* stream);
+
 /* Synchronizes the device and frees the batch (not the meshes). NULL is accepted. */
 gbd_status gbd_batch_destroy(gbd_batch* batch);
 

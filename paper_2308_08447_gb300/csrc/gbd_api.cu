@@ -654,33 +654,33 @@ static void extrap_weights(double c, float w[5]) {
   }
 }
 
-gbd_status gbd_llg_step_ex(gbd_mesh* m, float* mm, int nsteps, double dt, unsigned flags, void* stream) {
-  gbd_status s = ready(m);
-  if (s != GBD_OK) return s;
-  if (!ptr_ok(mm)) return fail(GBD_EINVAL, "m must be a non-NULL, 4-byte aligned device pointer");
-  if (nsteps < 0) return fail(GBD_EINVAL, "nsteps must be >= 0");
-  if (!(dt > 0) || !std::isfinite(dt)) return fail(GBD_EINVAL, "dt must be finite and > 0");
-  if (flags & ~(unsigned)(GBD_STEP_EXTRAP | GBD_STEP_CONTINUE)) return fail(GBD_EINVAL, "unknown flags");
-  if (nsteps == 0) return GBD_OK;
+// Allocates the mesh's extrapolation history on first use (never inside a stream capture).
+static gbd_status ensure_history(gbd_mesh* m) {
+  if (m->hist) return GBD_OK;
+  cudaError_t e = cudaMalloc(&m->hist, (size_t)5 * 3 * m->p.N * sizeof(float));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    m->hist = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? GBD_ENOMEM : GBD_ECUDA, "demag history allocation");
+  }
+  m->hist_count = 0;
+  return GBD_OK;
+}
+
+// The launch sequence of gbd_llg_step_ex on st (timed per launch when the mesh's timing is on).
+// Advances the mesh's extrapolation history state as the launches will; with GBD_STEP_EXTRAP
+// the history must exist.
+static void enqueue_llg_ex(gbd_mesh* m, float* mm, int nsteps, double dt, unsigned flags, cudaStream_t st) {
+  if (nsteps <= 0) return;
   const bool extrap = (flags & GBD_STEP_EXTRAP) != 0;
   const long long n3 = 3 * m->p.N;
   if (extrap) {
-    if (!m->hist) {
-      cudaError_t e = cudaMalloc(&m->hist, (size_t)5 * n3 * sizeof(float));
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        m->hist = nullptr;
-        return fail(e == cudaErrorMemoryAllocation ? GBD_ENOMEM : GBD_ECUDA, "demag history allocation");
-      }
-      m->hist_count = 0;
-    }
     if (!(flags & GBD_STEP_CONTINUE) || dt != m->hist_dt) m->hist_count = 0;
     m->hist_dt = dt;
   }
   float w_half[5], w_one[5];
   extrap_weights(0.5, w_half);
   extrap_weights(1.0, w_one);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   gbd::RowArgs a = row_args(m);
   a.dt = (float)dt;
   a.in = mm;
@@ -727,6 +727,21 @@ gbd_status gbd_llg_step_ex(gbd_mesh* m, float* mm, int nsteps, double dt, unsign
         timed(m, GBD_PASS_ROW_RK, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
     }
   }
+}
+
+gbd_status gbd_llg_step_ex(gbd_mesh* m, float* mm, int nsteps, double dt, unsigned flags, void* stream) {
+  gbd_status s = ready(m);
+  if (s != GBD_OK) return s;
+  if (!ptr_ok(mm)) return fail(GBD_EINVAL, "m must be a non-NULL, 4-byte aligned device pointer");
+  if (nsteps < 0) return fail(GBD_EINVAL, "nsteps must be >= 0");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(GBD_EINVAL, "dt must be finite and > 0");
+  if (flags & ~(unsigned)(GBD_STEP_EXTRAP | GBD_STEP_CONTINUE)) return fail(GBD_EINVAL, "unknown flags");
+  if (nsteps == 0) return GBD_OK;
+  if (flags & GBD_STEP_EXTRAP) {
+    s = ensure_history(m);
+    if (s != GBD_OK) return s;
+  }
+  enqueue_llg_ex(m, mm, nsteps, dt, flags, static_cast<cudaStream_t>(stream));
   return after_launch("gbd_llg_step");
 }
 
@@ -1042,6 +1057,10 @@ struct gbd_batch {
   std::vector<int> key_steps;
   std::vector<double> key_dt;
   std::vector<unsigned> key_version;
+  std::vector<unsigned> key_flags;
+  // extrapolation history state of each mesh before the captured run (part of the key) and
+  // after it (restored on every replay, which advances the history exactly as the capture did)
+  std::vector<std::array<double, 3>> key_hist, post_hist;
   cudaGraphExec_t exec = nullptr;
 };
 
@@ -1049,33 +1068,12 @@ namespace {
 constexpr int kBatchBranches = 32;
 
 // gbd_llg_step's launch sequence for one mesh on one stream (no timing events).
-void enqueue_llg(gbd_mesh* m, float* mm, int nsteps, double dt, cudaStream_t st) {
-  if (nsteps <= 0) return;
-  gbd::RowArgs a = row_args(m);
-  a.dt = (float)dt;
-  a.in = mm;
-  a.mode = gbd::ROW_FWD;
-  a.fwd_after = 1;
-  gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st);
-  a.m0 = mm;
-  a.m0_out = mm;
-  a.acc = m->acc;
-  for (int step = 0; step < nsteps; ++step) {
-    const bool last = (step == nsteps - 1);
-    const float* ms[4] = {mm, m->bufA, m->bufB, m->bufA};
-    float* mn[4] = {m->bufA, m->bufB, m->bufA, nullptr};
-    for (int stage = 0; stage < 4; ++stage) {
-      const bool tmp = m->timing;
-      m->timing = false;
-      enqueue_conv(m, st);
-      m->timing = tmp;
-      a.ms = ms[stage];
-      a.mnext = mn[stage];
-      a.mode = gbd::ROW_RK1 + stage;
-      a.fwd_after = (last && stage == 3) ? 0 : 1;
-      gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st);
-    }
-  }
+// gbd_llg_step_ex's launch sequence for one mesh on one stream, without timing events.
+void enqueue_llg(gbd_mesh* m, float* mm, int nsteps, double dt, unsigned flags, cudaStream_t st) {
+  const bool tmp = m->timing;
+  m->timing = false;
+  enqueue_llg_ex(m, mm, nsteps, dt, flags, st);
+  m->timing = tmp;
 }
 
 void destroy_batch(gbd_batch* b) {
@@ -1131,24 +1129,50 @@ extern "C" gbd_status gbd_batch_create(gbd_mesh* const* meshes, int count, gbd_b
   return GBD_OK;
 }
 
-extern "C" gbd_status gbd_batch_run(gbd_batch* b, float* const* m, const int* nsteps, const double* dt, void* stream) {
+static std::array<double, 3> hist_state(const gbd_mesh* m) {
+  return {(double)m->hist_head, (double)m->hist_count, m->hist_dt};
+}
+
+static void set_hist_state(gbd_mesh* m, const std::array<double, 3>& h) {
+  m->hist_head = (int)h[0];
+  m->hist_count = (int)h[1];
+  m->hist_dt = h[2];
+}
+
+extern "C" gbd_status gbd_batch_run_ex(gbd_batch* b, float* const* m, const int* nsteps, const double* dt,
+                                       const unsigned* flags, void* stream) {
   if (!b || !m || !nsteps || !dt) return fail(GBD_EINVAL, "NULL argument");
   const int n = (int)b->meshes.size();
+  std::vector<unsigned> fl(n, 0u);
   for (int i = 0; i < n; ++i) {
     if (!ptr_ok(m[i])) return fail(GBD_EINVAL, "m[" + std::to_string(i) + "] must be a non-NULL, 4-byte aligned device pointer");
     if (nsteps[i] < 0) return fail(GBD_EINVAL, "nsteps must be >= 0");
     if (!(dt[i] > 0) || !std::isfinite(dt[i])) return fail(GBD_EINVAL, "dt must be finite and > 0");
+    if (flags) fl[i] = flags[i];
+    if (fl[i] & ~(unsigned)(GBD_STEP_EXTRAP | GBD_STEP_CONTINUE)) return fail(GBD_EINVAL, "unknown flags");
   }
   gbd_status s = check_device(b->meshes[0]);
   if (s != GBD_OK) return s;
+  for (int i = 0; i < n; ++i)
+    if ((fl[i] & GBD_STEP_EXTRAP) && nsteps[i] > 0) {
+      s = ensure_history(b->meshes[i]);
+      if (s != GBD_OK) return s;
+    }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaStream_t og = b->origin;
   std::vector<unsigned> version(n);
-  for (int i = 0; i < n; ++i) version[i] = b->meshes[i]->version;
+  std::vector<std::array<double, 3>> pre(n);
+  for (int i = 0; i < n; ++i) {
+    version[i] = b->meshes[i]->version;
+    pre[i] = hist_state(b->meshes[i]);
+  }
   const bool same = b->exec && b->key_m == std::vector<float*>(m, m + n) &&
                     b->key_steps == std::vector<int>(nsteps, nsteps + n) &&
-                    b->key_dt == std::vector<double>(dt, dt + n) && b->key_version == version;
-  if (!same) {
+                    b->key_dt == std::vector<double>(dt, dt + n) && b->key_version == version &&
+                    b->key_flags == fl && b->key_hist == pre;
+  if (same) {
+    for (int i = 0; i < n; ++i) set_hist_state(b->meshes[i], b->post_hist[i]);
+  } else {
     if (b->exec) {
       cudaGraphExecDestroy(b->exec);
       b->exec = nullptr;
@@ -1159,7 +1183,7 @@ extern "C" gbd_status gbd_batch_run(gbd_batch* b, float* const* m, const int* ns
     cudaEventRecord(b->fork, og);
     const int nb = (int)b->branches.size();
     for (int j = 0; j < nb; ++j) cudaStreamWaitEvent(b->branches[j], b->fork, 0);
-    for (int i = 0; i < n; ++i) enqueue_llg(b->meshes[i], m[i], nsteps[i], dt[i], b->branches[i % nb]);
+    for (int i = 0; i < n; ++i) enqueue_llg(b->meshes[i], m[i], nsteps[i], dt[i], fl[i], b->branches[i % nb]);
     for (int j = 0; j < nb; ++j) {
       cudaEventRecord(b->join[j], b->branches[j]);
       cudaStreamWaitEvent(og, b->join[j], 0);
@@ -1170,12 +1194,17 @@ extern "C" gbd_status gbd_batch_run(gbd_batch* b, float* const* m, const int* ns
     if (e != cudaSuccess) {
       b->exec = nullptr;
       cudaGetLastError();
+      for (int i = 0; i < n; ++i) set_hist_state(b->meshes[i], pre[i]);
       return cuda_fail(e, "gbd_batch_run: graph capture");
     }
     b->key_m.assign(m, m + n);
     b->key_steps.assign(nsteps, nsteps + n);
     b->key_dt.assign(dt, dt + n);
     b->key_version = version;
+    b->key_flags = fl;
+    b->key_hist = pre;
+    b->post_hist.resize(n);
+    for (int i = 0; i < n; ++i) b->post_hist[i] = hist_state(b->meshes[i]);
   }
   // order the graph after the caller's earlier work on `stream`, and later work after it
   cudaEventRecord(b->ev_in, st);
@@ -1185,6 +1214,10 @@ extern "C" gbd_status gbd_batch_run(gbd_batch* b, float* const* m, const int* ns
   cudaEventRecord(b->ev_out, og);
   cudaStreamWaitEvent(st, b->ev_out, 0);
   return after_launch("gbd_batch_run");
+}
+
+extern "C" gbd_status gbd_batch_run(gbd_batch* b, float* const* m, const int* nsteps, const double* dt, void* stream) {
+  return gbd_batch_run_ex(b, m, nsteps, dt, nullptr, stream);
 }
 
 extern "C" gbd_status gbd_batch_destroy(gbd_batch* b) {

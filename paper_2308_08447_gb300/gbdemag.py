@@ -62,6 +62,7 @@ _SIG = {
     "gbd_mesh_set_tuning": [_P, ctypes.POINTER(_I)],
     "gbd_batch_create": [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)],
     "gbd_batch_run": [_P, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_D), _P],
+    "gbd_batch_run_ex": [_P, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_uint), _P],
     "gbd_batch_destroy": [_P],
     "gbd_mesh_set_timing": [_P, _I],
     "gbd_mesh_read_timing": [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)],
@@ -236,12 +237,16 @@ def gbd_batch_create(meshes):
     return out
 
 
-def gbd_batch_run(batch, m_list, shapes, nsteps, dts, stream=None):
+def gbd_batch_run(batch, m_list, shapes, nsteps, dts, stream=None, flags=None):
     n = len(m_list)
     ptrs = (ctypes.c_void_p * n)(*[_field_ptr(t, s, "m[%d]" % i).value for i, (t, s) in enumerate(zip(m_list, shapes))])
     steps = (ctypes.c_int * n)(*[int(v) for v in nsteps])
     dt = (ctypes.c_double * n)(*[float(v) for v in dts])
-    _check(load().gbd_batch_run(batch, ptrs, steps, dt, _stream_ptr(stream)))
+    if flags is None:
+        _check(load().gbd_batch_run(batch, ptrs, steps, dt, _stream_ptr(stream)))
+    else:
+        fl = (ctypes.c_uint * n)(*[int(v) for v in flags])
+        _check(load().gbd_batch_run_ex(batch, ptrs, steps, dt, fl, _stream_ptr(stream)))
 
 
 def gbd_batch_destroy(batch):
@@ -358,8 +363,9 @@ class Batch:
         self.meshes = list(meshes)
         self.handle = gbd_batch_create([m.handle for m in self.meshes])
 
-    def run(self, m_list, nsteps, dts, stream=None):
-        gbd_batch_run(self.handle, m_list, [m.shape for m in self.meshes], nsteps, dts, stream)
+    def run(self, m_list, nsteps, dts, stream=None, flags=None):
+        """flags: per-mesh GBD_STEP_* bits (None: plain RK4 for every mesh)."""
+        gbd_batch_run(self.handle, m_list, [m.shape for m in self.meshes], nsteps, dts, stream, flags)
 
     def close(self):
         if self.handle is not None:

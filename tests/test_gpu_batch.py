@@ -107,3 +107,30 @@ def test_batch_member_tracks_oracle(g):
     batch.close()
     for m in meshes:
         m.close()
+
+
+@pytest.mark.parametrize("chunk", [10, 7])
+def test_batch_with_extrapolation_equals_alone(chunk):
+    # per-mesh GBD_STEP_EXTRAP (+ GBD_STEP_CONTINUE after the first run): bit-identical to each
+    # mesh alone; chunk 10 replays the cached graph once the history is full, 7 re-captures
+    import torch
+    g = lib()
+    shapes = [(64, 48, 1), (32, 32, 4), (96, 32, 2)]
+    cell = (3e-9, 3e-9, 3e-9)
+    meshes = [g.Mesh(n, cell, 8e5, A_ex=1.3e-11, alpha=0.1) for n in shapes]
+    alone = [g.Mesh(n, cell, 8e5, A_ex=1.3e-11, alpha=0.1) for n in shapes]
+    m0 = [W.random_unit(n, 70 + i) for i, n in enumerate(shapes)]
+    mb = [torch.from_numpy(v).cuda() for v in m0]
+    ma = [torch.from_numpy(v).cuda() for v in m0]
+    batch = g.Batch(meshes)
+    for r in range(4):
+        flags = [g.GBD_STEP_EXTRAP | (g.GBD_STEP_CONTINUE if r else 0)] * len(shapes)
+        batch.run(mb, [chunk] * len(shapes), [1e-13] * len(shapes), flags=flags)
+        for mesh, m in zip(alone, ma):
+            mesh.llg_step(m, chunk, 1e-13, extrap=True, cont=r > 0)
+    torch.cuda.synchronize()
+    for a, b in zip(ma, mb):
+        assert torch.equal(a, b)
+    batch.close()
+    for mesh in meshes + alone:
+        mesh.close()
