@@ -308,6 +308,7 @@ def run_ours(args):
             result["extrapolated_demag"] = extrap
         if world == 1 and not args.no_cpu_baseline:
             result["cpu_baseline"] = cpu_baseline(spec, m0, repeats=4)
+            result["cpu_baseline_all_cores"] = cpu_baseline_all_cores(spec)
     mesh.close()
     if dist is not None:
         dist.barrier()
@@ -340,6 +341,46 @@ def cpu_baseline(spec, m0, repeats=1, Nf=None):
     return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d RK4 step(s) of the 1024x1024x1 film = %d demag evaluations (numpy FP64, "
                       "single-threaded FFT); %.1f s" % (repeats, 4 * repeats, t)}
+
+
+def _oracle_replica(q, barrier, repeats):
+    """One replica of the CPU baseline in its own process: set-up, wait for all replicas, then
+    `repeats` RK4 steps of the full film; puts the timed seconds on q."""
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    import numpy as np
+
+    from oracle import llg as L
+    from paper_2308_08447_gb300 import workloads as W
+    spec = W.thin_film()
+    m = W.vortex_noise(spec.n, spec.cell, spec.seed).astype(np.float64)
+    Nf = oracle_tensor(spec)
+    f = lambda v: L.rhs(v, Nf, spec.cell, spec.Ms, spec.A_ex, spec.alpha)
+    barrier.wait()
+    t0 = time.perf_counter()
+    for _ in range(repeats):
+        m = L.rk4_step(m, spec.dt, f)
+    q.put(time.perf_counter() - t0)
+
+
+def cpu_baseline_all_cores(spec, repeats=1):
+    """The same oracle on every host core at once: one independent replica per core (spawned
+    processes, one thread each), started together after their untimed set-up; the value is
+    the work of all replicas over the slowest replica's time."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    ctx = mp.get_context("spawn")
+    q, barrier = ctx.Queue(), ctx.Barrier(cores)
+    procs = [ctx.Process(target=_oracle_replica, args=(q, barrier, repeats)) for _ in range(cores)]
+    for p in procs:
+        p.start()
+    times = [q.get(timeout=900) for _ in procs]
+    for p in procs:
+        p.join()
+    value = cores * spec.cells * 4 * repeats / max(times) / 1e9
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d concurrent replicas x %d RK4 step(s) of the 1024x1024x1 film (numpy FP64, one thread "
+                      "each); slowest replica %.1f s" % (cores, repeats, max(times))}
 
 
 def run_batch(args):
