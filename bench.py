@@ -708,6 +708,19 @@ def run_switching(args):
         torch.cuda.synchronize()
         return torch.stack(rec).double().cpu().numpy(), e0.elapsed_time(e1) / 1e3, per * n_rec
 
+    def run_rkf(tol):
+        mm = mS.clone()
+        rec, dt, acc, rej = [], 100e-15, 0, 0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(n_rec):
+            dt, a_, r_ = mesh.run_rkf56(mm, interval, dt, tol)
+            acc, rej = acc + a_, rej + r_
+            rec.append(mm.mean(dim=(1, 2, 3)))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return torch.stack(rec).double().cpu().numpy(), e0.elapsed_time(e1) / 1e3, acc, rej
+
     ref, _, _ = run(25e-15, False)
     scaling = {}
     timing = {}
@@ -718,6 +731,12 @@ def run_switching(args):
             row["extrap" if extrap else "exact"] = float(np.linalg.norm(traj - ref, axis=1).sum() / n_rec)
             timing[(dt, extrap)] = (secs, steps)
         scaling["%g fs" % (dt * 1e15)] = row
+    adaptive = {}
+    for tol in (1e-4, 1e-5):
+        traj, secs_a, acc, rej = run_rkf(tol)
+        adaptive["tol %g" % tol] = {"eps": float(np.linalg.norm(traj - ref, axis=1).sum() / n_rec),
+                                    "accepted": acc, "rejected": rej, "mean_step_fs": round(t_end / acc * 1e15, 1),
+                                    "s": round(secs_a, 3)}
     secs, steps = timing[(100e-15, False)]
     xsecs, xsteps = timing[(100e-15, True)]
     mesh.close()
@@ -731,7 +750,7 @@ def run_switching(args):
                        "l2": "not flushed (1 ns of dynamics per run)"},
             "llg_steps_per_s": round(steps / secs, 1), "llg_steps_per_s_extrap": round(xsteps / xsecs, 1),
             "relax_s": round(relax_s, 2),
-            "eps_vs_25fs_exact": scaling, "mean_m_25fs_exact": samples}
+            "eps_vs_25fs_exact": scaling, "adaptive_rkf56": adaptive, "mean_m_25fs_exact": samples}
 
 
 def run_reference(args):

@@ -144,6 +144,23 @@ gbd_status gbd_llg_step(gbd_mesh* mesh, float* m, int nsteps, double dt, void* s
  *   start-up; valid only when m is that call's result, unchanged, and dt is the same (a
  *   different dt restarts the history). Without it every call starts a new history.
  * Other bits: GBD_EINVAL. */
+/* Adaptive RKF5(6) stepping (Sec. III names the Runge-Kutta-Fehlberg 5th-order method with
+ * 6th-order error estimation; its tableau is not in the paper): Fehlberg's eight-stage RK5(6)
+ * pair. A step evaluates eight demag + exchange + LLG slopes k_i at the stage states
+ * m + dt sum_j a_ij k_j, takes the fifth-order result m + dt sum_i b5_i k_i (renormalized per
+ * cell) and the error estimate err = dt max_cells |sum_i (b6_i - b5_i) k_i|.
+ * gbd_llg_rkf56_step: one step of size dt (> 0), always kept; *err receives the estimate.
+ * gbd_llg_run_rkf56: integrates from 0 to t_end (>= 0) starting with step *dt (> 0), accepting a
+ * step when err <= tol (> 0) and retrying otherwise, with the next size
+ * h min(5, max(0.2, 0.9 (tol/err)^(1/6))); the last step ends exactly at t_end. Stops early
+ * after max_steps (>= 1) attempts. On return *dt holds the next proposed size and
+ * *accepted / *rejected (either may be NULL) the step counts. Both calls wait for the stream
+ * after every step (the next size depends on the error); the first call allocates the stage
+ * buffers (108 bytes per cell). m: device [3][nz][ny][nx] unit vectors, in/out. */
+gbd_status gbd_llg_rkf56_step(gbd_mesh* mesh, float* m, double dt, double* err, void* stream);
+gbd_status gbd_llg_run_rkf56(gbd_mesh* mesh, float* m, double t_end, double* dt, double tol, int max_steps,
+                             int* accepted, int* rejected, void* stream);
+
 #define GBD_STEP_EXTRAP 1u
 #define GBD_STEP_CONTINUE 2u
 gbd_status gbd_llg_step_ex(gbd_mesh* mesh, float* m, int nsteps, double dt, unsigned flags, void* stream);

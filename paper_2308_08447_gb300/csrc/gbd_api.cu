@@ -1,6 +1,7 @@
 // C ABI of the demag convolution + exchange/LLG/RK4 library (declarations and contracts in
 // include/gbdemag.h). Host side: argument checks, planning, device buffers, the kernel
 // spectrum upload and the launch sequences of Eq. 1 (Sec. II) and of the RK4 time step.
+#include <algorithm>
 #include <array>
 #include <cmath>
 #include <cstdint>
@@ -49,6 +50,12 @@ struct gbd_mesh {
   int hist_count = 0, hist_head = 0;
   double hist_dt = 0.0;
   unsigned version = 0;     // bumped when launch arguments change (params, tuning): batch graphs re-capture
+  // RKF5(6) stepping (allocated on first use): 8 stage slopes [3][N] each, the step's result,
+  // the error word and its pinned host copy
+  float* rk_k = nullptr;
+  float* rk_m = nullptr;
+  unsigned* rk_err = nullptr;
+  unsigned* rk_err_host = nullptr;
   bool kernel_set = false;
   // optional per-launch timing: events[2i], events[2i+1] bracket launch i of class cls[i]
   bool timing = false;
@@ -190,6 +197,12 @@ static void free_mesh_buffers(gbd_mesh* m) {
   cudaFree(m->tw);
   cudaFree(m->hist);
   m->hist = nullptr;
+  cudaFree(m->rk_k);
+  cudaFree(m->rk_m);
+  cudaFree(m->rk_err);
+  cudaFreeHost(m->rk_err_host);
+  m->rk_k = m->rk_m = nullptr;
+  m->rk_err = m->rk_err_host = nullptr;
   m->S = m->T = nullptr;
   m->K = nullptr;
   m->acc = m->bufA = m->bufB = nullptr;
@@ -743,6 +756,150 @@ gbd_status gbd_llg_step_ex(gbd_mesh* m, float* mm, int nsteps, double dt, unsign
   }
   enqueue_llg_ex(m, mm, nsteps, dt, flags, static_cast<cudaStream_t>(stream));
   return after_launch("gbd_llg_step");
+}
+
+// ---- adaptive RKF5(6) (Sec. III) -------------------------------------------------------------
+// Fehlberg's eight-stage RK5(6) pair: rows a_(i+1),j of the stage matrix, fifth-order weights
+// b5 (the step's result) and sixth-order weights b6 (the error estimate).
+static const double kRkfA[8][7] = {
+    {0, 0, 0, 0, 0, 0, 0},
+    {1.0 / 6, 0, 0, 0, 0, 0, 0},
+    {4.0 / 75, 16.0 / 75, 0, 0, 0, 0, 0},
+    {5.0 / 6, -8.0 / 3, 5.0 / 2, 0, 0, 0, 0},
+    {-8.0 / 5, 144.0 / 25, -4.0, 16.0 / 25, 0, 0, 0},
+    {361.0 / 320, -18.0 / 5, 407.0 / 128, -11.0 / 80, 55.0 / 128, 0, 0},
+    {-11.0 / 640, 0, 11.0 / 256, -11.0 / 160, 11.0 / 256, 0, 0},
+    {93.0 / 640, -18.0 / 5, 803.0 / 256, -11.0 / 160, 99.0 / 256, 0, 1.0}};
+static const double kRkfB5[8] = {31.0 / 384, 0, 1125.0 / 2816, 9.0 / 32, 125.0 / 768, 5.0 / 66, 0, 0};
+static const double kRkfB6[8] = {7.0 / 1408, 0, 1125.0 / 2816, 9.0 / 32, 125.0 / 768, 0, 5.0 / 66, 5.0 / 66};
+static const double kRkfSafety = 0.9, kRkfFacMin = 0.2, kRkfFacMax = 5.0;
+
+static gbd_status ensure_rkf(gbd_mesh* m) {
+  if (m->rk_k) return GBD_OK;
+  const size_t n3 = (size_t)3 * m->p.N;
+  cudaError_t e = cudaMalloc(&m->rk_k, 8 * n3 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->rk_m, n3 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&m->rk_err, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMallocHost(&m->rk_err_host, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(m->rk_k);
+    cudaFree(m->rk_m);
+    cudaFree(m->rk_err);
+    m->rk_k = m->rk_m = nullptr;
+    m->rk_err = nullptr;
+    m->rk_err_host = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? GBD_ENOMEM : GBD_ECUDA, "RKF5(6) buffer allocation");
+  }
+  return GBD_OK;
+}
+
+// One RKF5(6) step of size h from mm: the normalized fifth-order result into m->rk_m and the
+// error estimate h max_cells |sum_i (b6_i - b5_i) k_i| into *err (waits for the stream).
+static gbd_status rkf_step(gbd_mesh* m, const float* mm, double h, cudaStream_t st, double* err) {
+  const size_t n3 = (size_t)3 * m->p.N;
+  float* k[8];
+  for (int i = 0; i < 8; ++i) k[i] = m->rk_k + i * n3;
+  gbd::RowArgs a = row_args(m);
+  a.in = mm;
+  a.mode = gbd::ROW_FWD;
+  a.fwd_after = 1;
+  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
+  float* stage_in[2] = {m->bufA, m->bufB};
+  const float* ms = mm;
+  for (int i = 0; i < 8; ++i) {
+    enqueue_conv(m, st);
+    a.mode = gbd::ROW_RKG;
+    a.ms = ms;
+    a.m0 = mm;
+    a.kout = k[i];
+    a.nk = i;
+    for (int j = 0; j < i; ++j) a.kin[j] = k[j];
+    if (i < 7) {
+      for (int j = 0; j <= i; ++j) a.kw[j] = (float)(h * kRkfA[i + 1][j]);
+      a.mnext = stage_in[i % 2];
+      a.fwd_after = 1;
+    } else {
+      a.mnext = nullptr;
+      a.fwd_after = 0;
+    }
+    timed(m, GBD_PASS_ROW_RK, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
+    ms = a.mnext;
+  }
+  gbd::RkfArgs f;
+  std::memset(&f, 0, sizeof(f));
+  f.N = m->p.N;
+  f.m = mm;
+  for (int i = 0; i < 8; ++i) {
+    f.k[i] = k[i];
+    f.b5dt[i] = (float)(h * kRkfB5[i]);
+    f.db[i] = (float)(kRkfB6[i] - kRkfB5[i]);
+  }
+  f.out = m->rk_m;
+  f.err_max = m->rk_err;
+  cudaError_t e = cudaMemsetAsync(m->rk_err, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return cuda_fail(e, "RKF5(6) step");
+  gbd::launch_rkf_final(f, st);
+  e = cudaMemcpyAsync(m->rk_err_host, m->rk_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "RKF5(6) step");
+  float ef;
+  std::memcpy(&ef, m->rk_err_host, sizeof(float));
+  *err = h * (double)ef;
+  return GBD_OK;
+}
+
+gbd_status gbd_llg_rkf56_step(gbd_mesh* m, float* mm, double dt, double* err, void* stream) {
+  gbd_status s = ready(m);
+  if (s != GBD_OK) return s;
+  if (!ptr_ok(mm) || !err) return fail(GBD_EINVAL, "m must be a 4-byte aligned device pointer and err non-NULL");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(GBD_EINVAL, "dt must be finite and > 0");
+  s = ensure_rkf(m);
+  if (s != GBD_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s = rkf_step(m, mm, dt, st, err);
+  if (s != GBD_OK) return s;
+  cudaError_t e = cudaMemcpyAsync(mm, m->rk_m, (size_t)3 * m->p.N * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gbd_llg_rkf56_step");
+  return after_launch("gbd_llg_rkf56_step");
+}
+
+gbd_status gbd_llg_run_rkf56(gbd_mesh* m, float* mm, double t_end, double* dt, double tol, int max_steps,
+                             int* accepted, int* rejected, void* stream) {
+  gbd_status s = ready(m);
+  if (s != GBD_OK) return s;
+  if (!ptr_ok(mm) || !dt) return fail(GBD_EINVAL, "m must be a 4-byte aligned device pointer and dt non-NULL");
+  if (!(t_end >= 0) || !std::isfinite(t_end)) return fail(GBD_EINVAL, "t_end must be finite and >= 0");
+  if (!(*dt > 0) || !std::isfinite(*dt)) return fail(GBD_EINVAL, "*dt must be finite and > 0");
+  if (!(tol > 0) || !std::isfinite(tol)) return fail(GBD_EINVAL, "tol must be finite and > 0");
+  if (max_steps < 1) return fail(GBD_EINVAL, "max_steps must be >= 1");
+  s = ensure_rkf(m);
+  if (s != GBD_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)3 * m->p.N * sizeof(float);
+  double t = 0.0, h_next = *dt;
+  int acc = 0, rej = 0;
+  while (t < t_end && acc + rej < max_steps) {
+    const double h = std::min(h_next, t_end - t);
+    double err = 0.0;
+    s = rkf_step(m, mm, h, st, &err);
+    if (s != GBD_OK) return s;
+    const double fac = err == 0.0 ? kRkfFacMax
+                                  : std::min(kRkfFacMax, std::max(kRkfFacMin, kRkfSafety * std::pow(tol / err, 1.0 / 6.0)));
+    h_next = h * fac;
+    if (err <= tol) {
+      cudaError_t e = cudaMemcpyAsync(mm, m->rk_m, bytes, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return cuda_fail(e, "gbd_llg_run_rkf56");
+      t += h;
+      ++acc;
+    } else {
+      ++rej;
+    }
+  }
+  *dt = h_next;
+  if (accepted) *accepted = acc;
+  if (rejected) *rejected = rej;
+  return after_launch("gbd_llg_run_rkf56");
 }
 
 gbd_status gbd_llg_step(gbd_mesh* m, float* mm, int nsteps, double dt, void* stream) {

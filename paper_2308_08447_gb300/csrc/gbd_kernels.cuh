@@ -28,6 +28,8 @@ enum RowMode : int {
   ROW_RK2 = 5,
   ROW_RK3 = 6,
   ROW_RK4 = 7,
+  ROW_RKG = 8,      // inverse + a general explicit RK stage: k = dm/dt at ms into kout, and the
+                    // next stage input m0 + sum_j kw[j] kin[j] + kw[nk] k (+ its forward)
 };
 
 // Block shapes per transform length L and tile variant v, shared by host planning and the
@@ -77,6 +79,24 @@ struct RowArgs {
   float hw[5];
   const float* hist[5];
   float* hrec;
+  // general explicit RK stage (ROW_RKG): kin[0..nk) are earlier stages' dm/dt, kw their
+  // weights dt a_(i+1),j, kw[nk] the weight of this stage's k; mnext may be null (last stage)
+  float* kout;
+  const float* kin[7];
+  float kw[8];
+  int nk;
+};
+
+// Final combination of an RKF5(6) step (Sec. III): m5 = normalize(m + sum_i b5dt[i] k_i) per
+// cell into out, and the largest |sum_i db[i] k_i| over cells into *err_max (float bits, >= 0).
+struct RkfArgs {
+  long long N;
+  const float* m;
+  const float* k[8];
+  float b5dt[8];
+  float db[8];
+  float* out;
+  unsigned* err_max;
 };
 
 struct ColArgs {
@@ -97,6 +117,7 @@ bool launch_row(int Lx, int var, int prec, const RowArgs& a, const float2* tw, c
 // An extrapolated RK4 stage with no forward transform after it (a.extrap = 1, a.fwd_after = 0):
 // the row kernel's epilogue alone, at full occupancy.
 void launch_extrap_stage(const RowArgs& a, cudaStream_t st);
+void launch_rkf_final(const RkfArgs& a, cudaStream_t st);
 bool launch_film_conv(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st);
 bool launch_y_fwd(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st);
 bool launch_y_inv(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st);

@@ -155,6 +155,28 @@ __device__ __forceinline__ bool epilogue_pair(const RowArgs& a, int mode, int z,
     lap[1][c] = a.cx * (cc.x - 2.f * cc.y + right) + a.cy * (ym.y - 2.f * cc.y + yp.y) + a.cz * (zm.y - 2.f * cc.y + zp.y);
   }
   float m0v[2][3] = {}, accv[2][3] = {};
+  if (mode == ROW_RKG) {
+    float res[2][3], ao[2][3];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) llg_update(a, ROW_RHS, hd[u], mv[u], lap[u], m0v[u], accv[u], mn[u], ao[u], res[u]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      *reinterpret_cast<float2*>(a.kout + c * N + idx) = make_float2(res[0][c], res[1][c]);
+      if (!a.mnext) continue;
+      float2 s = *reinterpret_cast<const float2*>(a.m0 + c * N + idx);
+      for (int j = 0; j < a.nk; ++j) {
+        const float2 kj = *reinterpret_cast<const float2*>(a.kin[j] + c * N + idx);
+        s.x = fmaf(a.kw[j], kj.x, s.x);
+        s.y = fmaf(a.kw[j], kj.y, s.y);
+      }
+      s.x = fmaf(a.kw[a.nk], res[0][c], s.x);
+      s.y = fmaf(a.kw[a.nk], res[1][c], s.y);
+      *reinterpret_cast<float2*>(a.mnext + c * N + idx) = s;
+      mn[0][c] = s.x;
+      mn[1][c] = s.y;
+    }
+    return a.mnext != nullptr;
+  }
   if (mode == ROW_RK2 || mode == ROW_RK3 || mode == ROW_RK4) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -222,6 +244,21 @@ __device__ __forceinline__ bool epilogue_cell(const RowArgs& a, int mode, int z,
              a.cz * (p[izp] - 2.f * mc + p[izm]);
   }
   float m0v[3] = {}, accv[3] = {};
+  if (mode == ROW_RKG) {
+    float res[3], ao[3];
+    llg_update(a, ROW_RHS, hd, mv, lap, m0v, accv, mn, ao, res);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      a.kout[c * N + idx] = res[c];
+      if (!a.mnext) continue;
+      float s = a.m0[c * N + idx];
+      for (int j = 0; j < a.nk; ++j) s = fmaf(a.kw[j], a.kin[j][c * N + idx], s);
+      s = fmaf(a.kw[a.nk], res[c], s);
+      a.mnext[c * N + idx] = s;
+      mn[c] = s;
+    }
+    return a.mnext != nullptr;
+  }
   if (mode == ROW_RK2 || mode == ROW_RK3 || mode == ROW_RK4) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -246,6 +283,41 @@ __device__ __forceinline__ bool epilogue_cell(const RowArgs& a, int mode, int z,
     }
   }
   return true;
+}
+
+// Final combination of an RKF5(6) step, one thread per cell, and the block's largest error
+// norm folded into *err_max (non-negative floats order like their bit patterns).
+__global__ void __launch_bounds__(256) rkf_final_kernel(const RkfArgs a) {
+  __shared__ float red[8];
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float e2 = 0.f;
+  if (i < a.N) {
+    float v[3], d[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      v[c] = a.m[c * a.N + i];
+      d[c] = 0.f;
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const float ks = a.k[s][c * a.N + i];
+        v[c] = fmaf(a.b5dt[s], ks, v[c]);
+        d[c] = fmaf(a.db[s], ks, d[c]);
+      }
+    }
+    const float inv = rsqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a.out[c * a.N + i] = v[c] * inv;
+    e2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e2 = fmaxf(e2, __shfl_xor_sync(0xffffffffu, e2, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float mx = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
+    atomicMax(a.err_max, __float_as_uint(sqrtf(mx)));
+  }
 }
 
 // Extrapolated RK4 stage without a transform (stages 2 and 3, and a last stage 4): the
@@ -605,6 +677,8 @@ static void set_vec8(RowArgs& a) {
   bool ok = al8(a.in) && al8(a.ms) && al8(a.m0) && al8(a.m0_out) && al8(a.acc) && al8(a.mnext) && al8(a.out) &&
             al8(a.hrec);
   for (int k = 0; k < 5; ++k) ok = ok && al8(a.hist[k]);
+  ok = ok && al8(a.kout);
+  for (int k = 0; k < 7; ++k) ok = ok && al8(a.kin[k]);
   a.vec8 = ok ? 1 : 0;
 }
 
@@ -612,6 +686,10 @@ bool launch_row(int Lx, int var, int prec, const RowArgs& a0, const float2* tw, 
   RowArgs a = a0;
   set_vec8(a);
   return row_dispatch(Lx, var, prec, &a, tw, st);
+}
+
+void launch_rkf_final(const RkfArgs& a, cudaStream_t st) {
+  rkf_final_kernel<<<(unsigned)((a.N + 255) / 256), 256, 0, st>>>(a);
 }
 
 void launch_extrap_stage(const RowArgs& a0, cudaStream_t st) {

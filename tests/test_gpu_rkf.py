@@ -1,0 +1,72 @@
+"""Adaptive RKF5(6) on the GPU (gbd_llg_rkf56_step / gbd_llg_run_rkf56) against the oracle's
+reading (oracle/rkf.py; Sec. III).
+
+With a tolerance that accepts every step the controller's step sizes are fixed (each next size
+is 5x the last, cut at t_end), so the GPU run and the oracle run take the same steps and end in
+the same state to FP32 accuracy; a single step's error estimate agrees; an adaptive run at a
+real tolerance stays close to a fine-step RK4 reference.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import lib, to_dev, to_host
+from oracle import llg as L
+from oracle import rkf as R
+from oracle import tensor as T
+from paper_2308_08447_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    return lib()
+
+
+CASES = [((32, 24, 2), (3e-9, 3e-9, 3e-9), (0.0, 0.0, 5e4)), ((64, 48, 1), (2e-9, 2e-9, 3e-9), (0.0, 0.0, 0.0)),
+         ((20, 12, 5), (4e-9, 3e-9, 2e-9), (1e4, 0.0, 0.0))]
+
+
+@pytest.mark.parametrize("n,cell,Hext", CASES)
+def test_fixed_sequence_tracks_oracle(g, n, cell, Hext):
+    Ms, A, alpha, dt = 8e5, 1.3e-11, 0.1, 5e-14
+    m = W.random_unit(n, 81)
+    mesh = g.Mesh(n, cell, Ms, A_ex=A, alpha=alpha, Hext=Hext)
+    md = to_dev(m)
+    nxt, acc, rej = mesh.run_rkf56(md, 4 * dt, dt, 1e30)
+    got = to_host(md)
+    mesh.close()
+    Nf = T.tensor_all_offsets(n, cell)
+    f = lambda v: L.rhs(v, Nf, cell, Ms, A, alpha, Hext)
+    want, acc_o, rej_o, nxt_o = R.run_adaptive(m.astype(np.float64), 4 * dt, dt, 1e30, f)
+    assert (acc, rej) == (acc_o, rej_o) == (2, 0) and abs(nxt - nxt_o) <= 1e-12 * nxt_o
+    assert np.abs(got - want).max() < 2e-5
+
+
+def test_single_step_error_estimate(g):
+    n, cell, Ms, A, alpha = (32, 32, 2), (3e-9, 3e-9, 3e-9), 8e5, 1.3e-11, 0.05
+    m = W.random_unit(n, 82)
+    mesh = g.Mesh(n, cell, Ms, A_ex=A, alpha=alpha)
+    md = to_dev(m)
+    err = mesh.rkf56_step(md, 1e-13)
+    got = to_host(md)
+    mesh.close()
+    Nf = T.tensor_all_offsets(n, cell)
+    want, err_o = R.rkf56_step(m.astype(np.float64), 1e-13, lambda v: L.rhs(v, Nf, cell, Ms, A, alpha))
+    # the estimate is dt |sum_i (b6_i - b5_i) k_i|, a difference of slopes that agree to about
+    # 1e-6 of dt |k| here (5e-7 against ~0.8): FP32 slopes (relative error ~1e-7) leave ~3 % of it
+    assert abs(err - err_o) <= 0.05 * err_o
+    assert np.abs(got - want).max() < 2e-5
+
+
+def test_adaptive_run_close_to_fine_reference(g):
+    n, cell, Ms, A, alpha = (32, 32, 1), (3e-9, 3e-9, 3e-9), 8e5, 1.3e-11, 0.2
+    m = W.vortex_noise(n, cell, 83)
+    mesh = g.Mesh(n, cell, Ms, A_ex=A, alpha=alpha)
+    md = to_dev(m)
+    _, acc, rej = mesh.run_rkf56(md, 5e-12, 1e-14, 1e-5)
+    got = to_host(md)
+    mesh.close()
+    Nf = T.tensor_all_offsets(n, cell)
+    ref = L.llg_run(m.astype(np.float64), 200, 2.5e-14, Nf, cell, Ms, A, alpha)
+    assert acc >= 1 and np.abs(got - ref).max() < 1e-4
