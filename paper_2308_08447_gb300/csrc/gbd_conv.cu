@@ -209,24 +209,29 @@ __global__ void __launch_bounds__(3 * W_ * L / GBD_E,
     };
     last_pass(std::false_type());
     __syncthreads();
-    // product at (column w, frequency kz): consecutive lanes take consecutive columns
-    for (int it = threadIdx.x; it < W * L; it += T) {
-      const int w = it % W, kz = it / W;
-      const long long q = q0 + w;
-      if (q >= Q) continue;
-      const int kx = (int)(q / Pyq);
-      const int ky = (int)(q - (long long)kx * Pyq);
-      int kyp = ky, kzp = kz;
-      float sy = 1.f, sz = 1.f;
-      if (Py > 1 && ky > Py / 2) {
-        kyp = Py - ky;
-        sy = -1.f;
-      }
+    // product at (column w, frequency kz): consecutive lanes take consecutive columns; T is a
+    // multiple of W, so each thread keeps one column and its (kx, ky) are worked out once
+    static_assert(T % W == 0, "a thread's product items share one column");
+    const int w = threadIdx.x % W;
+    const long long q = q0 + w;
+    const int kx = (int)(q / Pyq);
+    const int ky = (int)(q - (long long)kx * Pyq);
+    int kyp = ky;
+    float sy = 1.f;
+    if (Py > 1 && ky > Py / 2) {
+      kyp = Py - ky;
+      sy = -1.f;
+    }
+    const float* kcol = a.K3 + ((long long)kx * KY + kyp) * 6;
+    const long long kzs = (long long)a.Hx * KY * 6;      // kernel stride between kz planes
+    for (int kz = threadIdx.x / W; kz < L && q < Q; kz += T / W) {
+      int kzp = kz;
+      float sz = 1.f;
       if (kz > L / 2) {
         kzp = L - kz;
         sz = -1.f;
       }
-      const float* kp = a.K3 + (((long long)kzp * a.Hx + kx) * KY + kyp) * 6;
+      const float* kp = kcol + kzp * kzs;
       const float2 k01 = __ldg(reinterpret_cast<const float2*>(kp));
       const float2 k23 = __ldg(reinterpret_cast<const float2*>(kp + 2));
       const float2 k45 = __ldg(reinterpret_cast<const float2*>(kp + 4));
