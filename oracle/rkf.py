@@ -60,6 +60,63 @@ def next_dt(dt, err, tol):
     return dt * fac
 
 
+def rkf56_step_extrap(m, dt, demag, rest, history):
+    """One RKF5(6) step with the demag field extrapolated at stages 2-8 (Sec. III: a quintic
+    for RKF56). history: earlier accepted step starts as (t - t_n, H_d) pairs, newest first.
+    The field is evaluated at stage 1; with five earlier step starts, stages i >= 2 take the
+    quintic Lagrange polynomial through (0, H_d(t_n)) and those five, at time c_i dt.
+    Returns (m5, err, H_d(t_n))."""
+    from .extrap import lagrange_weights
+    hd1 = demag(m)
+    warm = len(history) >= 5
+    nodes = [0.0] + [t for t, _ in history[:5]]
+    fields = [hd1] + [h for _, h in history[:5]]
+    k = []
+    for i in range(8):
+        mi = m.copy()
+        for j, aij in enumerate(A[i]):
+            if aij != 0:
+                mi = mi + dt * float(aij) * k[j]
+        if i == 0:
+            hd = hd1
+        elif warm:
+            w = lagrange_weights(float(C[i]) * dt, nodes)
+            hd = sum(wk * fk for wk, fk in zip(w, fields))
+        else:
+            hd = demag(mi)
+        k.append(rest(mi, hd))
+    m5 = m.copy()
+    d = np.zeros_like(m)
+    for i in range(8):
+        if B5[i] != 0:
+            m5 = m5 + dt * float(B5[i]) * k[i]
+        if B6[i] != B5[i]:
+            d = d + float(B6[i] - B5[i]) * k[i]
+    err = dt * float(np.sqrt((d * d).sum(axis=0)).max())
+    return normalize(m5), err, hd1
+
+
+def run_adaptive_extrap(m, t_end, dt, tol, demag, rest, max_steps=100000):
+    """run_adaptive with the demag field extrapolated at stages 2-8 once five accepted step
+    starts are recorded; rest(m, H_d) gives dm/dt from the stage state and its demag field.
+    Returns (m, accepted, rejected, last dt proposal, demag evaluations)."""
+    t, acc, rej, nev = 0.0, 0, 0, 0
+    history = []                                 # (t_k, H_d(t_k)) of accepted step starts, newest first
+    while t < t_end and acc + rej < max_steps:
+        h = min(dt, t_end - t)
+        rel = [(tk - t, hk) for tk, hk in history]
+        m_new, err, hd1 = rkf56_step_extrap(m, h, demag, rest, rel)
+        nev += 1 if len(history) >= 5 else 8
+        dt = next_dt(h, err, tol)
+        if err <= tol:
+            history.insert(0, (t, hd1))
+            del history[5:]
+            m, t, acc = m_new, t + h, acc + 1
+        else:
+            rej += 1
+    return m, acc, rej, dt, nev
+
+
 def run_adaptive(m, t_end, dt, tol, f, max_steps=100000):
     """Adaptive RKF5(6) from t = 0 to t_end; returns (m, accepted, rejected, last dt proposal)."""
     t, acc, rej = 0.0, 0, 0

@@ -11,6 +11,7 @@ from fractions import Fraction as Fr
 
 import numpy as np
 
+from oracle import conv as C_
 from oracle import llg as L
 from oracle import rkf as R
 from oracle import tensor as T
@@ -115,3 +116,34 @@ def test_adaptive_run_meets_tolerance():
     # a looser tolerance takes fewer, larger steps
     _, acc2, _, _ = R.run_adaptive(m0, 2e-10, 1e-13, 1e-6, f)
     assert acc2 < acc
+
+
+def test_extrapolated_rkf_keeps_fifth_order_and_one_evaluation_per_step():
+    # quintic extrapolation at stages 2-8 (Sec. III): the demag field along the exact path is
+    # reproduced to O(dt^6), so fixed-step runs still converge at fifth order on the macrospin
+    from oracle import extrap as X
+    cell = (3e-9, 3e-9, 3e-9)
+    Nf = T.tensor_all_offsets((1, 1, 1), cell)
+    m0, _, exact = _macro()
+    demag = lambda v: C_.fft_conv(8e5 * v, Nf)
+    rest = lambda v, hd: L.llg_rhs(v, hd + L.exchange_field(v, cell, 8e5, 1.3e-11) + np.array([0.0, 0.0, 1e5])[:, None, None, None], 0.1)
+    # (steps of 2 ps and below: the five earlier steps the quintic spans then cover < 0.25 rad of
+    # the 2.2e10 rad/s precession; at 8 ps they cover ~1 rad and the extrapolation dominates)
+    errs = []
+    for dt in (2e-12, 1e-12, 5e-13):
+        steps = int(round(1.6e-10 / dt))
+        m, hist = m0, []
+        for n in range(steps):
+            m, _, hd1 = R.rkf56_step_extrap(m, dt, demag, rest, [(-(i + 1) * dt, h) for i, h in enumerate(hist)])
+            hist = [hd1] + hist[:4]
+        errs.append(np.linalg.norm(m[:, 0, 0, 0] - exact(steps * dt)))
+    for a, b in zip(errs, errs[1:]):
+        assert 20.0 < a / b < 48.0, errs
+    # the adaptive driver evaluates the field once per step after five accepted steps
+    _, acc, rej, _, nev = R.run_adaptive_extrap(m0, 2e-10, 1e-12, 1e-9, demag, rest)
+    assert acc > 5 and nev <= 8 * 5 + 8 * rej + (acc - 5)
+    # the weights at unequal nodes reproduce quintics exactly (the interpolation it relies on)
+    nodes = [0.0, -1.3, -2.1, -3.7, -4.2, -5.9]
+    for c in (0.25, 0.8, 1.0):
+        vals = [s ** 5 - 2 * s ** 3 + s for s in nodes]
+        assert abs(X.lagrange_weights(c, nodes) @ np.array(vals) - (c ** 5 - 2 * c ** 3 + c)) <= 1e-10
