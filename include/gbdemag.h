@@ -157,9 +157,15 @@ gbd_status gbd_llg_step(gbd_mesh* mesh, float* m, int nsteps, double dt, void* s
  * *accepted / *rejected (either may be NULL) the step counts. Both calls wait for the stream
  * after every step (the next size depends on the error); the first call allocates the stage
  * buffers (108 bytes per cell). m: device [3][nz][ny][nx] unit vectors, in/out. */
-gbd_status gbd_llg_rkf56_step(gbd_mesh* mesh, float* m, double dt, double* err, void* stream);
+/* flags (both calls): GBD_STEP_EXTRAP extrapolates the demag field at stages 2-8 (Sec. III: a
+ * quintic for RKF56, one demag evaluation per step): once five accepted step starts are
+ * recorded, a stage at time t + c_i dt takes the Lagrange quintic through this step's stage-1
+ * field and those five at their actual (unequal) times; exchange and Zeeman fields are still
+ * evaluated. GBD_STEP_CONTINUE keeps the recorded history of the previous call (m must be its
+ * result, unchanged). The history costs another 72 bytes per cell. */
+gbd_status gbd_llg_rkf56_step(gbd_mesh* mesh, float* m, double dt, double* err, unsigned flags, void* stream);
 gbd_status gbd_llg_run_rkf56(gbd_mesh* mesh, float* m, double t_end, double* dt, double tol, int max_steps,
-                             int* accepted, int* rejected, void* stream);
+                             int* accepted, int* rejected, unsigned flags, void* stream);
 
 #define GBD_STEP_EXTRAP 1u
 #define GBD_STEP_CONTINUE 2u

@@ -56,6 +56,13 @@ struct gbd_mesh {
   float* rk_m = nullptr;
   unsigned* rk_err = nullptr;
   unsigned* rk_err_host = nullptr;
+  // demag history of RKF5(6) with extrapolation: 6 slots of [3][N]; rk_ring holds the slots of
+  // the accepted step starts, newest first (rk_count valid), rk_ring_t their times relative to
+  // the current time; rk_pend receives the field of the step being tried
+  float* rk_hist = nullptr;
+  int rk_ring[5] = {0, 1, 2, 3, 4};
+  double rk_ring_t[5] = {0, 0, 0, 0, 0};
+  int rk_count = 0, rk_pend = 5;
   bool kernel_set = false;
   // optional per-launch timing: events[2i], events[2i+1] bracket launch i of class cls[i]
   bool timing = false;
@@ -201,6 +208,8 @@ static void free_mesh_buffers(gbd_mesh* m) {
   cudaFree(m->rk_m);
   cudaFree(m->rk_err);
   cudaFreeHost(m->rk_err_host);
+  cudaFree(m->rk_hist);
+  m->rk_hist = nullptr;
   m->rk_k = m->rk_m = nullptr;
   m->rk_err = m->rk_err_host = nullptr;
   m->S = m->T = nullptr;
@@ -723,6 +732,7 @@ static void enqueue_llg_ex(gbd_mesh* m, float* mm, int nsteps, double dt, unsign
       }
       if (warm && stage > 0) {
         a.extrap = 1;
+        a.nh = 5;
         const float* w = (stage == 3) ? w_one : w_half;
         for (int k = 0; k < 5; ++k) {
           a.hw[k] = w[k];
@@ -772,7 +782,36 @@ static const double kRkfA[8][7] = {
     {93.0 / 640, -18.0 / 5, 803.0 / 256, -11.0 / 160, 99.0 / 256, 0, 1.0}};
 static const double kRkfB5[8] = {31.0 / 384, 0, 1125.0 / 2816, 9.0 / 32, 125.0 / 768, 5.0 / 66, 0, 0};
 static const double kRkfB6[8] = {7.0 / 1408, 0, 1125.0 / 2816, 9.0 / 32, 125.0 / 768, 0, 5.0 / 66, 5.0 / 66};
+static const double kRkfC[8] = {0, 1.0 / 6, 4.0 / 15, 2.0 / 3, 4.0 / 5, 1.0, 0, 1.0};
 static const double kRkfSafety = 0.9, kRkfFacMin = 0.2, kRkfFacMax = 5.0;
+
+// An accepted step of size h: with extrapolation the pending field becomes the newest history
+// entry (at relative time 0 before the shift), the oldest slot becomes the next pending one,
+// and every recorded time moves back by h.
+static void rkf_accept(gbd_mesh* m, double h, bool extrap) {
+  if (!extrap) return;
+  const int freed = m->rk_ring[4];
+  for (int q = 4; q > 0; --q) {
+    m->rk_ring[q] = m->rk_ring[q - 1];
+    m->rk_ring_t[q] = m->rk_ring_t[q - 1] - h;
+  }
+  m->rk_ring[0] = m->rk_pend;
+  m->rk_ring_t[0] = -h;
+  m->rk_pend = freed;
+  if (m->rk_count < 5) ++m->rk_count;
+}
+
+static gbd_status ensure_rkf_history(gbd_mesh* m) {
+  if (m->rk_hist) return GBD_OK;
+  cudaError_t e = cudaMalloc(&m->rk_hist, (size_t)6 * 3 * m->p.N * sizeof(float));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    m->rk_hist = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? GBD_ENOMEM : GBD_ECUDA, "RKF5(6) demag history allocation");
+  }
+  m->rk_count = 0;
+  return GBD_OK;
+}
 
 static gbd_status ensure_rkf(gbd_mesh* m) {
   if (m->rk_k) return GBD_OK;
@@ -796,10 +835,22 @@ static gbd_status ensure_rkf(gbd_mesh* m) {
 
 // One RKF5(6) step of size h from mm: the normalized fifth-order result into m->rk_m and the
 // error estimate h max_cells |sum_i (b6_i - b5_i) k_i| into *err (waits for the stream).
-static gbd_status rkf_step(gbd_mesh* m, const float* mm, double h, cudaStream_t st, double* err) {
+static gbd_status rkf_step(gbd_mesh* m, const float* mm, double h, cudaStream_t st, double* err, bool extrap) {
   const size_t n3 = (size_t)3 * m->p.N;
   float* k[8];
   for (int i = 0; i < 8; ++i) k[i] = m->rk_k + i * n3;
+  // with five accepted step starts recorded, stages 2-8 take the quintic through them and this
+  // step's stage-1 field (recorded into the pending slot) instead of a convolution
+  const bool warm = extrap && m->rk_count >= 5;
+  double nodes[6] = {0.0};
+  const float* hsrc[6] = {nullptr};
+  if (extrap) {
+    hsrc[0] = m->rk_hist + (size_t)m->rk_pend * n3;
+    for (int q = 0; q < 5; ++q) {
+      nodes[q + 1] = m->rk_ring_t[q];
+      hsrc[q + 1] = m->rk_hist + (size_t)m->rk_ring[q] * n3;
+    }
+  }
   gbd::RowArgs a = row_args(m);
   a.in = mm;
   a.mode = gbd::ROW_FWD;
@@ -808,22 +859,44 @@ static gbd_status rkf_step(gbd_mesh* m, const float* mm, double h, cudaStream_t 
   float* stage_in[2] = {m->bufA, m->bufB};
   const float* ms = mm;
   for (int i = 0; i < 8; ++i) {
-    enqueue_conv(m, st);
     a.mode = gbd::ROW_RKG;
     a.ms = ms;
     a.m0 = mm;
     a.kout = k[i];
     a.nk = i;
     for (int j = 0; j < i; ++j) a.kin[j] = k[j];
+    a.hrec = (extrap && i == 0) ? m->rk_hist + (size_t)m->rk_pend * n3 : nullptr;
+    a.extrap = 0;
+    a.nh = 0;
+    if (warm && i > 0) {
+      a.extrap = 1;
+      a.nh = 6;
+      const double c = kRkfC[i] * h;
+      for (int q = 0; q < 6; ++q) {
+        double num = 1.0, den = 1.0;
+        for (int r = 0; r < 6; ++r)
+          if (r != q) {
+            num *= c - nodes[r];
+            den *= nodes[q] - nodes[r];
+          }
+        a.hw[q] = (float)(num / den);
+        a.hist[q] = hsrc[q];
+      }
+    }
     if (i < 7) {
       for (int j = 0; j <= i; ++j) a.kw[j] = (float)(h * kRkfA[i + 1][j]);
       a.mnext = stage_in[i % 2];
-      a.fwd_after = 1;
     } else {
       a.mnext = nullptr;
-      a.fwd_after = 0;
     }
-    timed(m, GBD_PASS_ROW_RK, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
+    // the next stage needs this stage's forward transform only when it convolves
+    a.fwd_after = (i < 7 && !warm) ? 1 : 0;
+    if (a.extrap) {
+      timed(m, GBD_PASS_EXTRAP, st, [&] { gbd::launch_extrap_stage(a, st); });
+    } else {
+      enqueue_conv(m, st);
+      timed(m, GBD_PASS_ROW_RK, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
+    }
     ms = a.mnext;
   }
   gbd::RkfArgs f;
@@ -849,23 +922,38 @@ static gbd_status rkf_step(gbd_mesh* m, const float* mm, double h, cudaStream_t 
   return GBD_OK;
 }
 
-gbd_status gbd_llg_rkf56_step(gbd_mesh* m, float* mm, double dt, double* err, void* stream) {
+// Validates RKF flags, allocates what they need and resets the history unless continued.
+static gbd_status rkf_prepare(gbd_mesh* m, unsigned flags) {
+  if (flags & ~(unsigned)(GBD_STEP_EXTRAP | GBD_STEP_CONTINUE)) return fail(GBD_EINVAL, "unknown flags");
+  gbd_status s = ensure_rkf(m);
+  if (s != GBD_OK) return s;
+  if (flags & GBD_STEP_EXTRAP) {
+    s = ensure_rkf_history(m);
+    if (s != GBD_OK) return s;
+    if (!(flags & GBD_STEP_CONTINUE)) m->rk_count = 0;
+  }
+  return GBD_OK;
+}
+
+gbd_status gbd_llg_rkf56_step(gbd_mesh* m, float* mm, double dt, double* err, unsigned flags, void* stream) {
   gbd_status s = ready(m);
   if (s != GBD_OK) return s;
   if (!ptr_ok(mm) || !err) return fail(GBD_EINVAL, "m must be a 4-byte aligned device pointer and err non-NULL");
   if (!(dt > 0) || !std::isfinite(dt)) return fail(GBD_EINVAL, "dt must be finite and > 0");
-  s = ensure_rkf(m);
+  s = rkf_prepare(m, flags);
   if (s != GBD_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  s = rkf_step(m, mm, dt, st, err);
+  const bool extrap = (flags & GBD_STEP_EXTRAP) != 0;
+  s = rkf_step(m, mm, dt, st, err, extrap);
   if (s != GBD_OK) return s;
+  rkf_accept(m, dt, extrap);
   cudaError_t e = cudaMemcpyAsync(mm, m->rk_m, (size_t)3 * m->p.N * sizeof(float), cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "gbd_llg_rkf56_step");
   return after_launch("gbd_llg_rkf56_step");
 }
 
 gbd_status gbd_llg_run_rkf56(gbd_mesh* m, float* mm, double t_end, double* dt, double tol, int max_steps,
-                             int* accepted, int* rejected, void* stream) {
+                             int* accepted, int* rejected, unsigned flags, void* stream) {
   gbd_status s = ready(m);
   if (s != GBD_OK) return s;
   if (!ptr_ok(mm) || !dt) return fail(GBD_EINVAL, "m must be a 4-byte aligned device pointer and dt non-NULL");
@@ -873,8 +961,9 @@ gbd_status gbd_llg_run_rkf56(gbd_mesh* m, float* mm, double t_end, double* dt, d
   if (!(*dt > 0) || !std::isfinite(*dt)) return fail(GBD_EINVAL, "*dt must be finite and > 0");
   if (!(tol > 0) || !std::isfinite(tol)) return fail(GBD_EINVAL, "tol must be finite and > 0");
   if (max_steps < 1) return fail(GBD_EINVAL, "max_steps must be >= 1");
-  s = ensure_rkf(m);
+  s = rkf_prepare(m, flags);
   if (s != GBD_OK) return s;
+  const bool extrap = (flags & GBD_STEP_EXTRAP) != 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bytes = (size_t)3 * m->p.N * sizeof(float);
   double t = 0.0, h_next = *dt;
@@ -882,7 +971,7 @@ gbd_status gbd_llg_run_rkf56(gbd_mesh* m, float* mm, double t_end, double* dt, d
   while (t < t_end && acc + rej < max_steps) {
     const double h = std::min(h_next, t_end - t);
     double err = 0.0;
-    s = rkf_step(m, mm, h, st, &err);
+    s = rkf_step(m, mm, h, st, &err, extrap);
     if (s != GBD_OK) return s;
     const double fac = err == 0.0 ? kRkfFacMax
                                   : std::min(kRkfFacMax, std::max(kRkfFacMin, kRkfSafety * std::pow(tol / err, 1.0 / 6.0)));
@@ -890,6 +979,7 @@ gbd_status gbd_llg_run_rkf56(gbd_mesh* m, float* mm, double t_end, double* dt, d
     if (err <= tol) {
       cudaError_t e = cudaMemcpyAsync(mm, m->rk_m, bytes, cudaMemcpyDeviceToDevice, st);
       if (e != cudaSuccess) return cuda_fail(e, "gbd_llg_run_rkf56");
+      rkf_accept(m, h, extrap);
       t += h;
       ++acc;
     } else {

@@ -72,12 +72,13 @@ struct RowArgs {
   int vec8;                 // the field pointers allow 8-byte accesses (set by launch_row)
   int per;                  // periodic axes (bit 0 x, 1 y, 2 z): the x transform has no zero
                             // half, and the exchange Laplacian wraps around
-  // demag extrapolation at RK4 sub-steps (Sec. III): with extrap the stage's demag field is
-  // sum_k hw[k] hist[k] over the step-start history (newest first) and no inverse transform
+  // demag extrapolation at RK sub-steps (Sec. III): with extrap the stage's demag field is
+  // sum_{k < nh} hw[k] hist[k] over the step-start history (newest first) and no inverse transform
   // runs; hrec, when set, receives the stage's demag field (hscale * H_d), [3][N]
   int extrap;
-  float hw[5];
-  const float* hist[5];
+  int nh;                   // history terms used (5 for RK4, 6 for RKF5(6))
+  float hw[6];
+  const float* hist[6];
   float* hrec;
   // general explicit RK stage (ROW_RKG): kin[0..nk) are earlier stages' dm/dt, kw their
   // weights dt a_(i+1),j, kw[nk] the weight of this stage's k; mnext may be null (last stage)

@@ -85,7 +85,8 @@ __device__ __forceinline__ void extrap_pair(const RowArgs& a, long long idx, flo
   for (int c = 0; c < 3; ++c) {
     float2 h2 = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < 6; ++k) {
+      if (k >= a.nh) break;
       const float2 hk = *reinterpret_cast<const float2*>(a.hist[k] + c * a.N + idx);
       h2.x = fmaf(a.hw[k], hk.x, h2.x);
       h2.y = fmaf(a.hw[k], hk.y, h2.y);
@@ -100,7 +101,10 @@ __device__ __forceinline__ void extrap_cell(const RowArgs& a, long long idx, flo
   for (int c = 0; c < 3; ++c) {
     float h = 0.f;
 #pragma unroll
-    for (int k = 0; k < 5; ++k) h = fmaf(a.hw[k], a.hist[k][c * a.N + idx], h);
+    for (int k = 0; k < 6; ++k) {
+      if (k >= a.nh) break;
+      h = fmaf(a.hw[k], a.hist[k][c * a.N + idx], h);
+    }
     hd[c] = h;
   }
 }
@@ -676,7 +680,7 @@ static void set_vec8(RowArgs& a) {
   auto al8 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; };
   bool ok = al8(a.in) && al8(a.ms) && al8(a.m0) && al8(a.m0_out) && al8(a.acc) && al8(a.mnext) && al8(a.out) &&
             al8(a.hrec);
-  for (int k = 0; k < 5; ++k) ok = ok && al8(a.hist[k]);
+  for (int k = 0; k < 6; ++k) ok = ok && al8(a.hist[k]);
   ok = ok && al8(a.kout);
   for (int k = 0; k < 7; ++k) ok = ok && al8(a.kin[k]);
   a.vec8 = ok ? 1 : 0;

@@ -50,8 +50,9 @@ _SIG = {
     "gbd_llg_step": [_P, _P, _I, _D, _P],
     "gbd_llg_step_ex": [_P, _P, _I, _D, ctypes.c_uint, _P],
     "gbd_mesh_set_params": [_P, ctypes.POINTER(_D), _D],
-    "gbd_llg_rkf56_step": [_P, _P, _D, ctypes.POINTER(_D), _P],
-    "gbd_llg_run_rkf56": [_P, _P, _D, ctypes.POINTER(_D), _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _P],
+    "gbd_llg_rkf56_step": [_P, _P, _D, ctypes.POINTER(_D), ctypes.c_uint, _P],
+    "gbd_llg_run_rkf56": [_P, _P, _D, ctypes.POINTER(_D), _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.c_uint,
+                          _P],
     "gbd_mesh_destroy": [_P],
     "gbd_tensor_at": [ctypes.POINTER(gbd_mesh_desc), _I, _I, _I, ctypes.POINTER(_D)],
     "gbd_plan_dims": [ctypes.POINTER(gbd_mesh_desc), ctypes.POINTER(_I)],
@@ -213,19 +214,20 @@ def gbd_mesh_set_params(mesh, Hext=None, alpha=None):
     _check(load().gbd_mesh_set_params(mesh, h, -1.0 if alpha is None else float(alpha)))
 
 
-def gbd_llg_rkf56_step(mesh, m, dt, shape, stream=None):
+def gbd_llg_rkf56_step(mesh, m, dt, shape, stream=None, flags=0):
     """One RKF5(6) step; returns the error estimate."""
     err = _D(0.0)
-    _check(load().gbd_llg_rkf56_step(mesh, _field_ptr(m, shape, "m"), float(dt), ctypes.byref(err),
+    _check(load().gbd_llg_rkf56_step(mesh, _field_ptr(m, shape, "m"), float(dt), ctypes.byref(err), int(flags),
                                      _stream_ptr(stream)))
     return err.value
 
 
-def gbd_llg_run_rkf56(mesh, m, t_end, dt, tol, shape, max_steps=1000000, stream=None):
+def gbd_llg_run_rkf56(mesh, m, t_end, dt, tol, shape, max_steps=1000000, stream=None, flags=0):
     """Adaptive RKF5(6) from 0 to t_end; returns (next dt, accepted, rejected)."""
     d, acc, rej = _D(float(dt)), _I(0), _I(0)
     _check(load().gbd_llg_run_rkf56(mesh, _field_ptr(m, shape, "m"), float(t_end), ctypes.byref(d), float(tol),
-                                    int(max_steps), ctypes.byref(acc), ctypes.byref(rej), _stream_ptr(stream)))
+                                    int(max_steps), ctypes.byref(acc), ctypes.byref(rej), int(flags),
+                                    _stream_ptr(stream)))
     return d.value, acc.value, rej.value
 
 
@@ -354,11 +356,14 @@ class Mesh:
             flags = (GBD_STEP_EXTRAP if extrap else 0) | (GBD_STEP_CONTINUE if cont else 0)
             gbd_llg_step_ex(self.handle, m, nsteps, dt, flags, self.shape, stream)
 
-    def rkf56_step(self, m, dt, stream=None):
-        return gbd_llg_rkf56_step(self.handle, m, dt, self.shape, stream)
+    def rkf56_step(self, m, dt, stream=None, extrap=False, cont=False):
+        flags = (GBD_STEP_EXTRAP if extrap else 0) | (GBD_STEP_CONTINUE if cont else 0)
+        return gbd_llg_rkf56_step(self.handle, m, dt, self.shape, stream, flags)
 
-    def run_rkf56(self, m, t_end, dt, tol, max_steps=1000000, stream=None):
-        return gbd_llg_run_rkf56(self.handle, m, t_end, dt, tol, self.shape, max_steps, stream)
+    def run_rkf56(self, m, t_end, dt, tol, max_steps=1000000, stream=None, extrap=False, cont=False):
+        """Adaptive RKF5(6) over [0, t_end]; returns (next dt, accepted, rejected)."""
+        flags = (GBD_STEP_EXTRAP if extrap else 0) | (GBD_STEP_CONTINUE if cont else 0)
+        return gbd_llg_run_rkf56(self.handle, m, t_end, dt, tol, self.shape, max_steps, stream, flags)
 
     def set_params(self, Hext=None, alpha=None):
         """Applied field (A/m) and/or damping of later calls (None keeps the current value)."""
