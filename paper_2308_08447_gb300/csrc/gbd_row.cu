@@ -79,14 +79,15 @@ __device__ __forceinline__ void llg_update(const RowArgs& a, int mode, const flo
   }
 }
 
-// Extrapolated demag field (sum_k hw[k] hist[k]) of cells idx, idx + 1.
-__device__ __forceinline__ void extrap_pair(const RowArgs& a, long long idx, float (&hd)[2][3]) {
+// Extrapolated demag field (sum_k hw[k] hist[k], k < NH) of cells idx, idx + 1. NH is a
+// template argument so that all history loads of a thread issue back to back.
+template <int NH>
+__device__ __forceinline__ void extrap_pair_n(const RowArgs& a, long long idx, float (&hd)[2][3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     float2 h2 = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      if (k >= a.nh) break;
+    for (int k = 0; k < NH; ++k) {
       const float2 hk = *reinterpret_cast<const float2*>(a.hist[k] + c * a.N + idx);
       h2.x = fmaf(a.hw[k], hk.x, h2.x);
       h2.y = fmaf(a.hw[k], hk.y, h2.y);
@@ -96,17 +97,30 @@ __device__ __forceinline__ void extrap_pair(const RowArgs& a, long long idx, flo
   }
 }
 
-__device__ __forceinline__ void extrap_cell(const RowArgs& a, long long idx, float (&hd)[3]) {
+template <int NH>
+__device__ __forceinline__ void extrap_cell_n(const RowArgs& a, long long idx, float (&hd)[3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     float h = 0.f;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      if (k >= a.nh) break;
-      h = fmaf(a.hw[k], a.hist[k][c * a.N + idx], h);
-    }
+    for (int k = 0; k < NH; ++k) h = fmaf(a.hw[k], a.hist[k][c * a.N + idx], h);
     hd[c] = h;
   }
+}
+
+// nh is 5 (quartic, RK4) or 6 (quintic, RKF5(6)); uniform over the grid.
+__device__ __forceinline__ void extrap_pair(const RowArgs& a, long long idx, float (&hd)[2][3]) {
+  if (a.nh == 6)
+    extrap_pair_n<6>(a, idx, hd);
+  else
+    extrap_pair_n<5>(a, idx, hd);
+}
+
+__device__ __forceinline__ void extrap_cell(const RowArgs& a, long long idx, float (&hd)[3]) {
+  if (a.nh == 6)
+    extrap_cell_n<6>(a, idx, hd);
+  else
+    extrap_cell_n<5>(a, idx, hd);
 }
 
 // Epilogue of the pair of cells (x0, x0 + 1), x0 even, at linear index idx (row of plane z at
