@@ -144,8 +144,8 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("gbd_fft.cuh", "gbd_tc.cuh", "gbd_kernels.cuh", "gbd_launch.cuh", "gbd_row.cu", "gbd_conv.cu",
-              "gbd_ypass.cu"):
+    for f in ("gbd_fft.cuh", "gbd_tc.cuh", "gbd_kernels.cuh", "gbd_launch.cuh", "gbd_row.cuh", "gbd_row.cu",
+              "gbd_conv.cuh", "gbd_conv.cu", "gbd_ypass.cu"):
         with open(os.path.join(ROOT, "paper_2308_08447_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -503,7 +503,7 @@ def run_serve(args):
 
 def run_3d(args):
     """512 x 512 x 64 cells of 4 nm, Ms = 8e5 A/m, random unit m: one demag evaluation and 100 RK4
-    steps with FP32 stages and with split-BF16 tensor-core stages. The demag error of each is
+    steps with FP32 stages and with split-BF16 and split-FP16 tensor-core stages. The demag error of each is
     taken against the FP64 oracle's FFT convolution of the full mesh (--oracle-3d); the 100-step
     error against the oracle's RK4 run is taken on a 64 x 64 x 8 mesh of the same material."""
     import numpy as np
@@ -519,10 +519,11 @@ def run_3d(args):
     m0 = W.random_unit(spec.n, spec.seed)
     res = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "data": "synthetic", "steps": args.steps, "warmup": args.warmup,
-           "config": {"workload": "3D 512x512x64, 4 nm cubes: 1 demag + %d RK4 steps, FP32 vs split-BF16" % nsteps}}
+           "config": {"workload": "3D 512x512x64, 4 nm cubes: 1 demag + %d RK4 steps, FP32 vs split-BF16 / split-FP16" % nsteps}}
     stream = torch.cuda.current_stream()
     H = {}
-    for name, prec in (("fp32", gbdemag.GBD_FP32), ("split_bf16", gbdemag.GBD_SPLIT_BF16)):
+    precs = (("fp32", gbdemag.GBD_FP32), ("split_bf16", gbdemag.GBD_SPLIT_BF16), ("split_fp16", gbdemag.GBD_SPLIT_FP16))
+    for name, prec in precs:
         mesh = gbdemag.Mesh(spec.n, spec.cell, spec.Ms, A_ex=spec.A_ex, alpha=spec.alpha, precision=prec)
         mesh.autotune()
         M = torch.from_numpy(spec.Ms * m0).cuda()
@@ -565,8 +566,9 @@ def run_3d(args):
                      "tuning": list(gbdemag.gbd_mesh_get_tuning(mesh.handle)), "passes": pass_info}
         res[name + "_m_after_100"] = m.cpu().numpy()
         mesh.close()
-    d = res.pop("split_bf16_m_after_100") - res.pop("fp32_m_after_100")
-    res["split_vs_fp32_m_after_100_max_abs"] = float(np.abs(d).max())
+    m32 = res.pop("fp32_m_after_100")
+    for name in ("split_bf16", "split_fp16"):
+        res[name]["m_after_100_max_abs_vs_fp32"] = float(np.abs(res.pop(name + "_m_after_100") - m32).max())
     res["value"] = res["fp32"]["llg_gcell_demag_per_s"]
     res["dtype"] = "f32"
     if args.oracle_3d:
@@ -575,7 +577,7 @@ def run_3d(args):
         t0 = time.perf_counter()
         Href = C.fft_conv((spec.Ms * m0).astype(np.float64), T.tensor_all_offsets(spec.n, spec.cell))
         nrm = np.sqrt((Href ** 2).sum(0)).max()
-        for name in ("fp32", "split_bf16"):
+        for name, _ in precs:
             res[name]["demag_e_inf_vs_fp64_oracle"] = float(np.sqrt(((H[name] - Href) ** 2).sum(0)).max() / nrm)
         res["oracle_s"] = round(time.perf_counter() - t0, 1)
     # 100 steps against the FP64 oracle on a 64 x 64 x 8 mesh of the same material
@@ -585,7 +587,7 @@ def run_3d(args):
     ms0 = W.random_unit(small, spec.seed)
     Nf = T.tensor_all_offsets(small, spec.cell)
     want = L.llg_run(ms0.astype(np.float64), nsteps, spec.dt, Nf, spec.cell, spec.Ms, spec.A_ex, spec.alpha)
-    for name, prec in (("fp32", gbdemag.GBD_FP32), ("split_bf16", gbdemag.GBD_SPLIT_BF16)):
+    for name, prec in precs:
         mesh = gbdemag.Mesh(small, spec.cell, spec.Ms, A_ex=spec.A_ex, alpha=spec.alpha, precision=prec)
         m = torch.from_numpy(ms0).cuda()
         mesh.llg_step(m, nsteps, spec.dt)

@@ -48,11 +48,14 @@ typedef enum {
   GBD_EUNSUPPORTED = 7  /* mesh larger than the supported padded lengths */
 } gbd_status;
 
-/* Arithmetic of the FFT stages. GBD_FP32 (default): every stage in FP32. GBD_SPLIT_BF16:
+/* Arithmetic of the FFT stages (Sec. II on halving the transfer precision only after
+ * normalization, applied here to the DFT stages). GBD_FP32 (default): every stage in FP32. GBD_SPLIT_BF16:
  * every radix-16 DFT stage runs on the tensor cores as dense products of two-term BF16
  * operands (hi + lo, three products, FP32 accumulation); twiddles, smaller radices, the
  * kernel product and the LLG update stay FP32; stated error bound e_inf <= 1e-4 on H_d.
- * GBD_SPLIT_FP16 is reserved (gbd_mesh_create answers GBD_EUNSUPPORTED). */
+ * GBD_SPLIT_FP16: the same with FP16 halves, each butterfly's inputs first scaled by a power
+ * of two into [0.5, 1) (FP16's range) and its outputs scaled back; stated bound e_inf <= 1e-5.
+ * Any other value: GBD_EINVAL. */
 typedef enum { GBD_FP32 = 0, GBD_SPLIT_BF16 = 1, GBD_SPLIT_FP16 = 2 } gbd_precision;
 
 /* Mesh and material. Sizes: 1 <= nx <= 4096, 1 <= ny <= 2048, 1 <= nz <= 2048. */

@@ -119,6 +119,10 @@ bool make_plan(int nx, int ny, int nz, int per, Plan& p, const char** why) {
     *why = "a periodic x axis needs nx >= 2";
     return false;
   }
+  if (((per & 2) && ny == 2) || ((per & 4) && nz == 2)) {
+    *why = "a periodic y or z axis needs 1 or at least 4 cells";
+    return false;
+  }
   p.nx = nx;
   p.ny = ny;
   p.nz = nz;
@@ -169,8 +173,8 @@ static gbd_status check_desc(const gbd_mesh_desc* d, gbd::Plan& p) {
   if (!(d->gamma >= 0) || !std::isfinite(d->gamma)) return fail(GBD_EINVAL, "gamma must be finite and >= 0");
   for (int i = 0; i < 3; ++i)
     if (!std::isfinite(d->Hext[i])) return fail(GBD_EINVAL, "Hext must be finite");
-  if (d->precision != GBD_FP32 && d->precision != GBD_SPLIT_BF16)
-    return fail(GBD_EUNSUPPORTED, "precision must be GBD_FP32 or GBD_SPLIT_BF16");
+  if (d->precision != GBD_FP32 && d->precision != GBD_SPLIT_BF16 && d->precision != GBD_SPLIT_FP16)
+    return fail(GBD_EINVAL, "precision must be GBD_FP32, GBD_SPLIT_BF16 or GBD_SPLIT_FP16");
   if (d->flags & ~(unsigned)(GBD_FLAG_PBC_X | GBD_FLAG_PBC_Y | GBD_FLAG_PBC_Z))
     return fail(GBD_EINVAL, "unknown flags");
   const int per = (int)(d->flags & 7u);
@@ -178,7 +182,7 @@ static gbd_status check_desc(const gbd_mesh_desc* d, gbd::Plan& p) {
     return fail(GBD_EINVAL, "pbc_images must be in [1, " + std::to_string(kMaxImages) + "] with a periodic axis");
   if (!gbd::make_plan(d->nx, d->ny, d->nz, per, p, &why)) return fail(GBD_EUNSUPPORTED, why);
   p.images = per ? d->pbc_images : 0;
-  p.prec = (d->precision == GBD_SPLIT_BF16) ? 1 : 0;
+  p.prec = (d->precision == GBD_SPLIT_BF16) ? 1 : (d->precision == GBD_SPLIT_FP16) ? 2 : 0;
   return GBD_OK;
 }
 
@@ -409,12 +413,17 @@ gbd_status gbd_mesh_create(const gbd_mesh_desc* desc, gbd_mesh** out) {
   }
   // shared-memory attributes of this mesh's kernels (both tile variants), set now so that
   // later launches, also inside a stream capture, need no configuration call
-  gbd::prepare_row(p.Lx, p.prec);
+  bool have = gbd::prepare_row(p.Lx, p.prec);
   if (p.film) {
-    gbd::prepare_film_conv(p.Py, p.prec);
+    have = have && gbd::prepare_film_conv(p.Py, p.prec);
   } else {
-    gbd::prepare_z_conv(p.Pz, p.prec);
-    if (p.ny > 1) gbd::prepare_y_passes(p.Py, p.prec);
+    have = have && gbd::prepare_z_conv(p.Pz, p.prec);
+    if (p.ny > 1) have = have && gbd::prepare_y_passes(p.Py, p.prec);
+  }
+  if (!have) {
+    free_mesh_buffers(m);
+    delete m;
+    return fail(GBD_EUNSUPPORTED, "no kernel instantiated for these transform lengths");
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) {

@@ -113,7 +113,8 @@ struct ColArgs {
 
 // Launchers dispatch on the transform length (a power of two) and the tile variant; they
 // return false for a length without an instantiation.
-// prec: 0 FP32 stages; 1 radix-16 stages on the tensor cores in split BF16 (gbd_tc.cuh).
+// prec: 0 FP32 stages; 1 / 2 radix-16 stages on the tensor cores in split BF16 / split FP16
+// (gbd_tc.cuh).
 bool launch_row(int Lx, int var, int prec, const RowArgs& a, const float2* tw, cudaStream_t st);
 // An extrapolated RK4 stage with no forward transform after it (a.extrap = 1, a.fwd_after = 0):
 // the row kernel's epilogue alone, at full occupancy.

@@ -1,14 +1,21 @@
-// Radix-16 Stockham pass with the 16-point DFT on the tensor cores, split BF16 (hi + lo) with
-// FP32 accumulation -- the optional precision variant of the FFT stages.
+// Radix-16 Stockham pass with the 16-point DFT on the tensor cores, split into two 16-bit
+// halves (hi + lo) with FP32 accumulation -- the optional precision variants of the FFT stages:
+// PREC = 1 splits into BF16, PREC = 2 into FP16.
 //
 // A butterfly's DFT is the real 32 x 32 product  [Yr; Yi] = [C, -sS; sS, C] [Xr; Xi]  with
 // C_qr = cos(2 pi q r / 16), S_qr = sin(2 pi q r / 16) and s the transform sign. Both operands
-// are split, A = Ah + Al and X = Xh + Xl with Ah = bf16(A), Al = bf16(A - Ah) (likewise X), and
-// Y ~= Ah Xh + Ah Xl + Al Xh in FP32 (the dropped Al Xl is below 2^-16 of the terms); the
-// representation error of each operand is about 2^-16 relative, the Sec. II rule of halving
-// precision "with normalization" needs no scale here because BF16 keeps FP32's exponent range.
+// are split, A = Ah + Al and X = Xh + Xl with Ah = h(A), Al = h(A - Ah) (likewise X, h the
+// rounding to the 16-bit type), and Y ~= Ah Xh + Ah Xl + Al Xh in FP32; the dropped Al Xl is
+// below 2^-16 (BF16) or 2^-22 (FP16) of the terms.
+// * BF16 keeps FP32's exponent range, so the data need no scaling; each operand is represented
+//   to about 2^-16 relative.
+// * FP16 has 11 significant bits but a range of about 6e-8 .. 65504, so each butterfly's 32 real
+//   inputs are first scaled by a power of two that brings their largest magnitude into
+//   [0.5, 1) (the Sec. II rule of halving the precision only after normalization) and its 32
+//   outputs are scaled back; both scalings are exact. An operand is then represented to about
+//   2^-22 of the butterfly's largest input.
 //
-// mma.sync.m16n8k16 (BF16 in, FP32 accumulate): a warp takes 8 butterflies (the n = 8 columns)
+// mma.sync.m16n8k16 (16-bit in, FP32 accumulate): a warp takes 8 butterflies (the n = 8 columns)
 // per group and 4 groups per pass, the same 32 butterflies its threads take in the FP32 pass.
 // With g = lane / 4 and t = lane % 4, lane holds for butterfly n = g the inputs r in
 // {2t, 2t+1, 2t+8, 2t+9} (B fragment rows: k-tile 0 = real parts, k-tile 1 = imaginary parts)
@@ -17,32 +24,56 @@
 // forward pass and to the outputs in an adjoint pass, exactly as in the FP32 pass.
 #pragma once
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "gbd_fft.cuh"
 
 namespace gbd {
 
-// bits of a bfloat16x2 with lo in the low half
-__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<unsigned*>(&v);
+// bits of a pair of 16-bit values (PREC 1: bfloat16, 2: half) with lo in the low half
+template <int PREC>
+__device__ __forceinline__ unsigned pack16(float lo, float hi) {
+  if constexpr (PREC == 1) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<unsigned*>(&v);
+  } else {
+    __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<unsigned*>(&v);
+  }
 }
 
-// x = hi + lo in bf16 pairs: (a, b) -> hi bits, lo bits
+// x = hi + lo in 16-bit pairs: (a, b) -> hi bits, lo bits
+template <int PREC>
 __device__ __forceinline__ void split2(float a, float b, unsigned& hi, unsigned& lo) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-  const float ra = a - __bfloat162float(h.x);
-  const float rb = b - __bfloat162float(h.y);
-  hi = *reinterpret_cast<const unsigned*>(&h);
-  lo = pack_bf16(ra, rb);
+  float ha, hb;
+  if constexpr (PREC == 1) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    ha = __low2float(h);
+    hb = __high2float(h);
+    hi = *reinterpret_cast<const unsigned*>(&h);
+  } else {
+    const __half2 h = __floats2half2_rn(a, b);
+    ha = __low2float(h);
+    hb = __high2float(h);
+    hi = *reinterpret_cast<const unsigned*>(&h);
+  }
+  lo = pack16<PREC>(a - ha, b - hb);
 }
 
-__device__ __forceinline__ void mma_bf16(float* d, const unsigned* a, unsigned b0, unsigned b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+template <int PREC>
+__device__ __forceinline__ void mma16(float* d, const unsigned* a, unsigned b0, unsigned b1) {
+  if constexpr (PREC == 1)
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+  else
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 // cos / sin of pi m / 8, m in [0, 16)
@@ -67,7 +98,7 @@ __device__ __forceinline__ float dft16_real(int row, int col) {
 }
 
 // A fragments of the split matrix: frag[mt][kt][hi/lo][4 registers]
-template <int S>
+template <int S, int PREC>
 struct Dft16Frags {
   unsigned f[2][2][2][4];
   __device__ __forceinline__ void build(int lane) {
@@ -82,14 +113,14 @@ struct Dft16Frags {
                             dft16_real<S>(r0, c0 + 8), dft16_real<S>(r0, c0 + 9),
                             dft16_real<S>(r0 + 8, c0 + 8), dft16_real<S>(r0 + 8, c0 + 9)};
 #pragma unroll
-        for (int i = 0; i < 4; ++i) split2(v[2 * i], v[2 * i + 1], f[mt][kt][0][i], f[mt][kt][1][i]);
+        for (int i = 0; i < 4; ++i) split2<PREC>(v[2 * i], v[2 * i + 1], f[mt][kt][0][i], f[mt][kt][1][i]);
       }
   }
 };
 
 // Radix-16 pass (forward: loads j + r L/16, stores (j-k) 16 + k + q Ns; adjoint: reverse),
 // block of exactly LINES * L / 16 threads, like stockham_pass.
-template <int S, bool ADJ, int L, int Ns, int LINES, bool LF, bool SYNC_MID, class LD, class ST>
+template <int PREC, int S, bool ADJ, int L, int Ns, int LINES, bool LF, bool SYNC_MID, class LD, class ST>
 __device__ __forceinline__ void stockham_pass_tc(const float2* __restrict__ tw, LD ld, ST st) {
   constexpr int R = 16;
   constexpr int LR = L / R;
@@ -123,16 +154,31 @@ __device__ __forceinline__ void stockham_pass_tc(const float2* __restrict__ tw, 
     }
   }
   if (SYNC_MID) __syncthreads();
-  Dft16Frags<S> A;
+  Dft16Frags<S, PREC> A;
   A.build(lane);
 #pragma unroll
   for (int grp = 0; grp < 4; ++grp) {
+    // FP16: butterfly g's inputs sit on lanes 4g .. 4g+3; scale them by 2^-e, e the binary
+    // exponent of their largest magnitude (frexp: max = f 2^e, f in [0.5, 1); e = 0 for zero)
+    int e = 0;
+    if constexpr (PREC == 2) {
+      float mx = 0.f;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) mx = fmaxf(mx, fmaxf(fabsf(x[grp][i].x), fabsf(x[grp][i].y)));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+      frexpf(mx, &e);
+      e = max(e, -125);   // a subnormal maximum keeps the scale 2^125 finite
+      const float sc = ldexpf(1.f, -e);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) x[grp][i] = cscale(x[grp][i], sc);
+    }
     // B fragments: k-tile 0 real parts, k-tile 1 imaginary parts; rows (r) 2t, 2t+1 | 2t+8, 2t+9
     unsigned bh[2][2], bl[2][2];
-    split2(x[grp][0].x, x[grp][1].x, bh[0][0], bl[0][0]);
-    split2(x[grp][2].x, x[grp][3].x, bh[0][1], bl[0][1]);
-    split2(x[grp][0].y, x[grp][1].y, bh[1][0], bl[1][0]);
-    split2(x[grp][2].y, x[grp][3].y, bh[1][1], bl[1][1]);
+    split2<PREC>(x[grp][0].x, x[grp][1].x, bh[0][0], bl[0][0]);
+    split2<PREC>(x[grp][2].x, x[grp][3].x, bh[0][1], bl[0][1]);
+    split2<PREC>(x[grp][0].y, x[grp][1].y, bh[1][0], bl[1][0]);
+    split2<PREC>(x[grp][2].y, x[grp][3].y, bh[1][1], bl[1][1]);
     float y[2][4];
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
@@ -140,9 +186,9 @@ __device__ __forceinline__ void stockham_pass_tc(const float2* __restrict__ tw, 
       for (int i = 0; i < 4; ++i) y[mt][i] = 0.f;
 #pragma unroll
       for (int kt = 0; kt < 2; ++kt) {
-        mma_bf16(y[mt], A.f[mt][kt][1], bh[kt][0], bh[kt][1]);   // Al Xh
-        mma_bf16(y[mt], A.f[mt][kt][0], bl[kt][0], bl[kt][1]);   // Ah Xl
-        mma_bf16(y[mt], A.f[mt][kt][0], bh[kt][0], bh[kt][1]);   // Ah Xh
+        mma16<PREC>(y[mt], A.f[mt][kt][1], bh[kt][0], bh[kt][1]);   // Al Xh
+        mma16<PREC>(y[mt], A.f[mt][kt][0], bl[kt][0], bl[kt][1]);   // Ah Xl
+        mma16<PREC>(y[mt], A.f[mt][kt][0], bh[kt][0], bh[kt][1]);   // Ah Xh
       }
     }
     // outputs: q in {g, g+8} of butterflies n in {2t, 2t+1}: (Re, Im) = (y[0][.], y[1][.])
@@ -151,10 +197,13 @@ __device__ __forceinline__ void stockham_pass_tc(const float2* __restrict__ tw, 
       int line, j;
       map(warp * 32 + grp * 8 + 2 * t + c, line, j);
       const int k = j % Ns;
+      float usc = 1.f;
+      if constexpr (PREC == 2) usc = ldexpf(1.f, __shfl_sync(0xffffffffu, e, 4 * (2 * t + c)));
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int q = g + 8 * h;
         float2 v = make_float2(y[0][2 * h + c], y[1][2 * h + c]);
+        if constexpr (PREC == 2) v = cscale(v, usc);
         if (ADJ && Ns > 1 && q > 0) v = cmul(v, twiddle_at<S>(tw, NR, (q * k) & (NR - 1)));
         st(line, ADJ ? j + q * LR : (j - k) * R + k + q * Ns, v);
       }
@@ -163,12 +212,13 @@ __device__ __forceinline__ void stockham_pass_tc(const float2* __restrict__ tw, 
 }
 
 // ---- pass selection by precision -------------------------------------------------------------
-// PREC = 0: FP32 everywhere. PREC = 1: every radix-16 pass on the tensor cores (split BF16).
+// PREC = 0: FP32 everywhere. PREC = 1 / 2: every radix-16 pass on the tensor cores, split
+// BF16 / split FP16.
 
 template <int PREC, int S, bool ADJ, int L, int R, int Ns, int LINES, bool LF, bool SYNC_MID, class LD, class ST>
 __device__ __forceinline__ void pass_any(const float2* __restrict__ tw, LD ld, ST st) {
   if constexpr (PREC != 0 && R == 16)
-    stockham_pass_tc<S, ADJ, L, Ns, LINES, LF, SYNC_MID>(tw, ld, st);
+    stockham_pass_tc<PREC, S, ADJ, L, Ns, LINES, LF, SYNC_MID>(tw, ld, st);
   else
     stockham_pass<S, ADJ, L, R, Ns, LINES, LF, SYNC_MID>(tw, ld, st);
 }
@@ -178,7 +228,7 @@ __device__ __forceinline__ void pass_sm_any(float2* sm, const float2* __restrict
   if constexpr (PREC != 0 && R == 16) {
     auto ld = [&](int line, int i) { return sm[line * LS + pad(i)]; };
     auto st = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
-    stockham_pass_tc<S, ADJ, L, Ns, LINES, LF, true>(tw, ld, st);
+    stockham_pass_tc<PREC, S, ADJ, L, Ns, LINES, LF, true>(tw, ld, st);
   } else {
     stockham_pass_sm<S, ADJ, L, R, Ns, LINES, LF, LS>(sm, tw);
   }

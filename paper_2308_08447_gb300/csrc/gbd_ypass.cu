@@ -66,11 +66,12 @@ static void ypass_launch_t(const ColArgs* a, const float2* tw, cudaStream_t st) 
   if (a) y_pass_kernel<L, C, INV, PREC><<<(unsigned)((a->lines_total + C - 1) / C), T, smem, st>>>(*a, tw);
 }
 
-// prec < 0 (with a == nullptr) prepares both precisions
+// prec < 0 (with a == nullptr) prepares every precision
 template <int L, int C, bool INV>
 static void ypass_launch_p(int prec, const ColArgs* a, const float2* tw, cudaStream_t st) {
   if (prec <= 0) ypass_launch_t<L, C, INV, 0>(a, tw, st);
-  if (prec != 0) ypass_launch_t<L, C, INV, 1>(a, tw, st);
+  if (prec == 1 || prec < 0) ypass_launch_t<L, C, INV, 1>(a, tw, st);
+  if (prec == 2 || prec < 0) ypass_launch_t<L, C, INV, 2>(a, tw, st);
 }
 
 #define GBD_Y_CASE(L)                                             \

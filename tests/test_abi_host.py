@@ -196,7 +196,7 @@ def test_caller_tensor_checks(g):
 # ---- periodic boundary conditions ----------------------------------------------------------
 
 @pytest.mark.parametrize("n,pbc,images", [((16, 8, 1), (True, True, False), 3), ((16, 12, 4), (True, False, False), 2),
-                                          ((8, 8, 4), (False, False, True), 2), ((4, 8, 2), (True, True, True), 1)])
+                                          ((8, 8, 4), (False, False, True), 2), ((4, 8, 4), (True, True, True), 1)])
 def test_periodic_spectrum_matches_oracle(g, n, pbc, images):
     from oracle import pbc as B
     cell = (2e-9, 3e-9, 2.5e-9)
@@ -232,7 +232,21 @@ def test_periodic_desc_checks(g):
     with pytest.raises(g.GbdError) as ei:
         g.gbd_plan_dims(d)
     assert ei.value.status == g.GBD_EINVAL
+    for n, pbc in (((16, 2, 1), (True, True, False)), ((8, 8, 2), (False, False, True))):
+        with pytest.raises(g.GbdError) as ei:      # no length-2 y or z transforms
+            g.gbd_plan_dims(g.make_desc(n, cell, 8e5, pbc=pbc, pbc_images=2))
+        assert ei.value.status == g.GBD_EUNSUPPORTED
     with pytest.raises(g.GbdError) as ei:          # caller tensors are for open boundaries
         g.gbd_kernel_spectrum_from_tensor_host(g.make_desc((4, 4, 1), cell, 8e5, pbc=(True, True, False),
                                                            pbc_images=1), np.zeros((6, 1, 7, 7)))
     assert ei.value.status == g.GBD_EUNSUPPORTED
+
+
+def test_precision_values(g):
+    cell = (2e-9, 2e-9, 2e-9)
+    for prec in (g.GBD_FP32, g.GBD_SPLIT_BF16, g.GBD_SPLIT_FP16):
+        assert g.gbd_plan_dims(g.make_desc((64, 32, 4), cell, 8e5, precision=prec))[:3] == (128, 64, 8)
+    for prec in (-1, 3):
+        with pytest.raises(g.GbdError) as ei:
+            g.gbd_plan_dims(g.make_desc((64, 32, 4), cell, 8e5, precision=prec))
+        assert ei.value.status == g.GBD_EINVAL
