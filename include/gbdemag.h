@@ -45,7 +45,7 @@ typedef enum {
   GBD_ESTATE = 4,       /* call order: e.g. gbd_demag before gbd_set_kernel */
   GBD_ETIMEOUT = 5,     /* a bounded device-side wait gave up (batched path) */
   GBD_EBUDGET = 6,      /* admission refused: the request does not fit the memory budget */
-  GBD_EUNSUPPORTED = 7  /* mesh larger than the supported padded lengths */
+  GBD_EUNSUPPORTED = 7  /* mesh size or transform length without a kernel, or a call the mesh cannot take */
 } gbd_status;
 
 /* Arithmetic of the FFT stages (Sec. II on halving the transfer precision only after
