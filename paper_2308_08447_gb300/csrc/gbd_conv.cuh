@@ -111,6 +111,8 @@ __global__ void __launch_bounds__(3 * C_ * L / GBD_E, min_blocks_film(3 * C_ * L
   if constexpr (NP <= 1) {
     run_fused(gld, gst);
   } else {
+    // The zero half of a y line is skipped by gld / gst alone: the half transforms that the z
+    // convolution uses (HALF passes) measured 2 us slower in this 56-register kernel (spills).
     pass_any<PREC, -1, false, L, radix_at(L, true, 0), 1, LINES, false, false>(tw, gld, sst);
     __syncthreads();
     fwd_passes_smem<-1, L, true, LINES, false, LS, 1, NP - 1, PREC>(sm, tw);
@@ -192,7 +194,12 @@ __global__ void __launch_bounds__(3 * W_ * L / GBD_E,
   if constexpr (NP == 1) {
     run_fused(gld, gst);
   } else {
-    pass_any<PREC, -1, false, L, radix_at(L, true, 0), 1, LINES, true, false>(tw, gld, sst);
+    // open z (Pz >= 2 nz): zero upper half in, cropped out; periodic z (Pz = nz): whole lines
+    const bool half = 2 * nz <= L;
+    if (half)
+      pass_any<PREC, -1, false, L, radix_at(L, true, 0), 1, LINES, true, false, true>(tw, gld, sst);
+    else
+      pass_any<PREC, -1, false, L, radix_at(L, true, 0), 1, LINES, true, false>(tw, gld, sst);
     __syncthreads();
     fwd_passes_smem<-1, L, true, LINES, true, LS, 1, NP - 1, PREC>(sm, tw);
     // The last forward pass, the product and the first adjoint pass as three in-place phases
@@ -212,8 +219,10 @@ __global__ void __launch_bounds__(3 * W_ * L / GBD_E,
     };
     last_pass(std::false_type());
     __syncthreads();
-    // product at (column w, frequency kz): consecutive lanes take consecutive columns; T is a
-    // multiple of W, so each thread keeps one column and its (kx, ky) are worked out once
+    // product at (column w, frequencies kz and Pz - kz): consecutive lanes take consecutive
+    // columns; T is a multiple of W, so each thread keeps one column and its (kx, ky) are worked
+    // out once. The stored kernel at kz' = kz serves both kz and Pz - kz (the latter with the
+    // z-odd components xz, yz negated), so an item loads it once for the pair.
     static_assert(T % W == 0, "a thread's product items share one column");
     const int w = threadIdx.x % W;
     const long long q = q0 + w;
@@ -227,29 +236,31 @@ __global__ void __launch_bounds__(3 * W_ * L / GBD_E,
     }
     const float* kcol = a.K3 + ((long long)kx * KY + kyp) * 6;
     const long long kzs = (long long)a.Hx * KY * 6;      // kernel stride between kz planes
-    for (int kz = threadIdx.x / W; kz < L && q < Q; kz += T / W) {
-      int kzp = kz;
-      float sz = 1.f;
-      if (kz > L / 2) {
-        kzp = L - kz;
-        sz = -1.f;
-      }
-      const float* kp = kcol + kzp * kzs;
+    for (int kz = threadIdx.x / W; kz <= L / 2 && q < Q; kz += T / W) {
+      const float* kp = kcol + kz * kzs;
       const float2 k01 = __ldg(reinterpret_cast<const float2*>(kp));
       const float2 k23 = __ldg(reinterpret_cast<const float2*>(kp + 2));
       const float2 k45 = __ldg(reinterpret_cast<const float2*>(kp + 4));
       const float kxx = k01.x, kyy = k01.y, kzz = k23.x;
-      const float kxy = sy * k23.y, kxz = sz * k45.x, kyz = sy * sz * k45.y;
-      const float2 m0 = sld(w, kz), m1 = sld(W + w, kz), m2 = sld(2 * W + w, kz);
-      sst(w, kz, make_float2(kxx * m0.x + kxy * m1.x + kxz * m2.x, kxx * m0.y + kxy * m1.y + kxz * m2.y));
-      sst(W + w, kz, make_float2(kxy * m0.x + kyy * m1.x + kyz * m2.x, kxy * m0.y + kyy * m1.y + kyz * m2.y));
-      sst(2 * W + w, kz, make_float2(kxz * m0.x + kyz * m1.x + kzz * m2.x, kxz * m0.y + kyz * m1.y + kzz * m2.y));
+      const float kxy = sy * k23.y, kxz0 = k45.x, kyz0 = sy * k45.y;
+      auto apply = [&](int z, float sz) {
+        const float kxz = sz * kxz0, kyz = sz * kyz0;
+        const float2 m0 = sld(w, z), m1 = sld(W + w, z), m2 = sld(2 * W + w, z);
+        sst(w, z, make_float2(kxx * m0.x + kxy * m1.x + kxz * m2.x, kxx * m0.y + kxy * m1.y + kxz * m2.y));
+        sst(W + w, z, make_float2(kxy * m0.x + kyy * m1.x + kyz * m2.x, kxy * m0.y + kyy * m1.y + kyz * m2.y));
+        sst(2 * W + w, z, make_float2(kxz * m0.x + kyz * m1.x + kzz * m2.x, kxz * m0.y + kyz * m1.y + kzz * m2.y));
+      };
+      apply(kz, 1.f);
+      if (kz > 0 && kz < L / 2) apply(L - kz, -1.f);
     }
     __syncthreads();
     last_pass(std::true_type());
     __syncthreads();
     adj_passes_smem<1, L, true, LINES, true, LS, NP - 1, 1, PREC>(sm, tw);
-    pass_any<PREC, 1, true, L, radix_at(L, true, 0), 1, LINES, true, false>(tw, sld, gst);
+    if (half)
+      pass_any<PREC, 1, true, L, radix_at(L, true, 0), 1, LINES, true, false, true>(tw, sld, gst);
+    else
+      pass_any<PREC, 1, true, L, radix_at(L, true, 0), 1, LINES, true, false>(tw, sld, gst);
   }
 }
 

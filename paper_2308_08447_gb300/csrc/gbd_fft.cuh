@@ -162,6 +162,65 @@ __device__ __forceinline__ void dft(float2* x) {
   }
 }
 
+// exp(S 2 pi i n / R) for R in {4, 8, 16} and 0 < n < R/2, from the literal constants of dft16
+template <int S, int R>
+__device__ __forceinline__ float2 wr(int n) {
+  const float c[8] = {1.0f, 0.92387953251128675613f, 0.70710678118654752440f, 0.38268343236508977173f,
+                      0.0f, -0.38268343236508977173f, -0.70710678118654752440f, -0.92387953251128675613f};
+  const float s[8] = {0.0f, 0.38268343236508977173f, 0.70710678118654752440f, 0.92387953251128675613f,
+                      1.0f, 0.92387953251128675613f, 0.70710678118654752440f, 0.38268343236508977173f};
+  const int q = n * (16 / R);   // angle 2 pi n / R = q pi / 8
+  return make_float2(c[q], S * s[q]);
+}
+
+// DFT_R (sign S) of x whose entries R/2 .. R-1 are zero; only x[0, R/2) are read. With H = R/2:
+//   X[2m] = DFT_H(x)[m],  X[2m+1] = DFT_H(x[n] w_R^n)[m],  w_R = exp(S 2 pi i / R).
+// The first pass of a transform whose upper half is zero padding (Ns = 1) needs no twiddles, so
+// this is the whole butterfly there.
+template <int R, int S>
+__device__ __forceinline__ void dft_half_in(float2* x) {
+  constexpr int H = R / 2;
+  if constexpr (H == 1) {
+    x[1] = x[0];
+  } else {
+    float2 e[H], o[H];
+#pragma unroll
+    for (int n = 0; n < H; ++n) {
+      e[n] = x[n];
+      o[n] = (n == 0) ? x[0] : (4 * n == R) ? cmul_i<S>(x[n]) : cmul(x[n], wr<S, R>(n));
+    }
+    dft<H, S>(e);
+    dft<H, S>(o);
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+      x[2 * m] = e[m];
+      x[2 * m + 1] = o[m];
+    }
+  }
+}
+
+// The first R/2 outputs of DFT_R (sign S) of x: X[q] = E[q] + w_R^q O[q], q < R/2, with E, O the
+// DFT_(R/2) of the even and odd entries (the first half of dft16's combination); x[R/2, R) are
+// left undefined. The last adjoint pass of a cropped transform (Ns = 1) keeps only these.
+template <int R, int S>
+__device__ __forceinline__ void dft_half_out(float2* x) {
+  constexpr int H = R / 2;
+  if constexpr (H == 1) {
+    x[0] = cadd(x[0], x[1]);
+  } else {
+    float2 e[H], o[H];
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      e[i] = x[2 * i];
+      o[i] = x[2 * i + 1];
+    }
+    dft<H, S>(e);
+    dft<H, S>(o);
+#pragma unroll
+    for (int q = 0; q < H; ++q) x[q] = cadd(e[q], (q == 0) ? o[0] : cmul(o[q], wr<S, R>(q)));
+  }
+}
+
 // v[r] *= exp(S 2 pi i r k / (Ns R)) for r in [1, R): loads w, w^2, w^4, w^8 and forms each
 // other power right before use (w^3 = w w^2, w^(8+r) = w^r w^8, ...), so at most the base
 // powers and one product are live next to the data.
@@ -213,9 +272,13 @@ __device__ __forceinline__ void butterfly(float2* v, int k, const float2* __rest
 // (line, j): LF puts consecutive b on consecutive lines, otherwise on consecutive j.
 // Forward: loads at j + r L/R, stores at (j-k) R + k + q Ns. Adjoint: the reverse.
 // LD(line, pos) -> float2, ST(line, pos, v). SYNC_MID separates loads from stores when the
-// pass works in place.
-template <int S, bool ADJ, int L, int R, int Ns, int LINES, bool LF, bool SYNC_MID, class LD, class ST>
+// pass works in place. HALF (first pass, Ns = 1): forward, positions >= L/2 hold zeros and are
+// not read (dft_half_in); adjoint, positions >= L/2 are not needed and not written
+// (dft_half_out). LD and ST must still be valid there (the tensor-core pass ignores HALF).
+template <int S, bool ADJ, int L, int R, int Ns, int LINES, bool LF, bool SYNC_MID, bool HALF = false, class LD,
+          class ST>
 __device__ __forceinline__ void stockham_pass(const float2* __restrict__ tw, LD ld, ST st) {
+  static_assert(!HALF || Ns == 1, "the half transforms are the Ns = 1 pass");
   constexpr int LR = L / R;
   constexpr int NB = GBD_E / R;
   constexpr int T = LINES * L / GBD_E;
@@ -236,16 +299,22 @@ __device__ __forceinline__ void stockham_pass(const float2* __restrict__ tw, LD 
     bj[i] = j;
     const int k = j % Ns;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[i][r] = ld(line, ADJ ? (j - k) * R + k + r * Ns : j + r * LR);
+    for (int r = 0; r < ((HALF && !ADJ) ? R / 2 : R); ++r) v[i][r] = ld(line, ADJ ? (j - k) * R + k + r * Ns : j + r * LR);
   }
   if (SYNC_MID) __syncthreads();
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
     const int j = bj[i];
     const int k = j % Ns;
-    butterfly<S, R, Ns, ADJ>(v[i], k, tw);
+    if constexpr (HALF && ADJ)
+      dft_half_out<R, S>(v[i]);
+    else if constexpr (HALF)
+      dft_half_in<R, S>(v[i]);
+    else
+      butterfly<S, R, Ns, ADJ>(v[i], k, tw);
 #pragma unroll
-    for (int q = 0; q < R; ++q) st(bl[i], ADJ ? j + q * LR : (j - k) * R + k + q * Ns, v[i][q]);
+    for (int q = 0; q < ((HALF && ADJ) ? R / 2 : R); ++q)
+      st(bl[i], ADJ ? j + q * LR : (j - k) * R + k + q * Ns, v[i][q]);
   }
 }
 

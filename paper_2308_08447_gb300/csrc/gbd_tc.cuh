@@ -215,12 +215,14 @@ __device__ __forceinline__ void stockham_pass_tc(const float2* __restrict__ tw, 
 // PREC = 0: FP32 everywhere. PREC = 1 / 2: every radix-16 pass on the tensor cores, split
 // BF16 / split FP16.
 
-template <int PREC, int S, bool ADJ, int L, int R, int Ns, int LINES, bool LF, bool SYNC_MID, class LD, class ST>
+// HALF: see stockham_pass (the tensor-core pass reads and writes every position through LD / ST).
+template <int PREC, int S, bool ADJ, int L, int R, int Ns, int LINES, bool LF, bool SYNC_MID, bool HALF = false,
+          class LD, class ST>
 __device__ __forceinline__ void pass_any(const float2* __restrict__ tw, LD ld, ST st) {
   if constexpr (PREC != 0 && R == 16)
     stockham_pass_tc<PREC, S, ADJ, L, Ns, LINES, LF, SYNC_MID>(tw, ld, st);
   else
-    stockham_pass<S, ADJ, L, R, Ns, LINES, LF, SYNC_MID>(tw, ld, st);
+    stockham_pass<S, ADJ, L, R, Ns, LINES, LF, SYNC_MID, HALF>(tw, ld, st);
 }
 
 template <int PREC, int S, bool ADJ, int L, int R, int Ns, int LINES, bool LF, int LS>

@@ -52,9 +52,6 @@ __global__ void __launch_bounds__(C_ * L / GBD_E, min_blocks(C_ * L / GBD_E))
   }
 }
 
-// 3D z convolution: block = W consecutive columns q of [3][nz][Q], lines c * W + w,
-// interleaved (consecutive threads take consecutive columns).
-
 // ---- launchers -------------------------------------------------------------------------------
 
 // a == nullptr only prepares the kernel (shared-memory attribute), without a launch.
