@@ -153,7 +153,7 @@ bool make_plan(int nx, int ny, int nz, int per, Plan& p, const char** why) {
   p.bytes_T = (!p.film && ny > 1) ? (size_t)3 * nz * p.Hx * p.Py * sizeof(float2) : 0;
   p.bytes_K = p.film ? (size_t)p.Hx * p.Ky * sizeof(float4) : (size_t)p.Hx * p.Ky * p.Kz * 6 * sizeof(float);
   p.bytes_state = (size_t)3 * 3 * p.N * sizeof(float);
-  p.bytes_tw = (size_t)2 * GBD_TW_LEN * sizeof(float2);
+  p.bytes_tw = (size_t)(2 * GBD_TW_LEN + GBD_TC_FRAG_F2) * sizeof(float2);
   return true;
 }
 
@@ -399,13 +399,19 @@ gbd_status gbd_mesh_create(const gbd_mesh_desc* desc, gbd_mesh** out) {
   }
   // twiddle levels: exp(-2 pi i m / N) at index N + m for N = 1, 2, 4, ..., GBD_TW_LEN and
   // m < N, FP64 on the host, rounded to FP32 (index 0 is unused)
+  // (the split DFT-16 fragment tables after them are written on the device below)
   std::vector<float2> tw(2 * GBD_TW_LEN, make_float2(1.f, 0.f));
   for (int N = 1; N <= GBD_TW_LEN; N *= 2)
     for (int k = 0; k < N; ++k) {
       const double ang = -2.0 * 3.14159265358979323846264338327950288 * (double)k / N;
       tw[N + k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
     }
-  e = cudaMemcpy(m->tw, tw.data(), p.bytes_tw, cudaMemcpyHostToDevice);
+  e = cudaMemcpy(m->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    gbd::launch_dft16_frags(m->tw + 2 * GBD_TW_LEN, nullptr);
+    e = cudaStreamSynchronize(nullptr);
+    if (e == cudaSuccess) e = cudaGetLastError();
+  }
   if (e != cudaSuccess) {
     free_mesh_buffers(m);
     delete m;

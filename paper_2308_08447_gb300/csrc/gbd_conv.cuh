@@ -48,7 +48,8 @@ __device__ __forceinline__ void fused_item(int line0, int lstride, int j, const 
 
 // film: one block = C columns kx, three components each, lines = c * C + cc.
 template <int L, int C_, int PREC>
-__global__ void __launch_bounds__(3 * C_ * L / GBD_E, min_blocks_film(3 * C_ * L / GBD_E))
+__global__ void __launch_bounds__(3 * C_ * L / GBD_E,
+                                  PREC == 0 ? min_blocks_film(3 * C_ * L / GBD_E) : min_blocks(3 * C_ * L / GBD_E))
     film_conv_kernel(ColArgs a, const float2* __restrict__ tw) {
   constexpr int C = C_;
   constexpr int LINES = 3 * C;

@@ -32,6 +32,10 @@
 
 #define GBD_TW_LEN 8192
 #define GBD_E 16
+// After the 2 GBD_TW_LEN twiddle entries the same buffer holds the tensor-core passes' split
+// DFT-16 fragments (gbd_tc.cuh): 4 tables (sign x 16-bit type) of 32 registers x 32 lanes of
+// 32 bits, i.e. 2048 float2 slots.
+#define GBD_TC_FRAG_F2 2048
 
 namespace gbd {
 

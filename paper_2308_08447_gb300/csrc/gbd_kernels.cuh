@@ -120,6 +120,9 @@ bool launch_row(int Lx, int var, int prec, const RowArgs& a, const float2* tw, c
 // the row kernel's epilogue alone, at full occupancy.
 void launch_extrap_stage(const RowArgs& a, cudaStream_t st);
 void launch_rkf_final(const RkfArgs& a, cudaStream_t st);
+// Writes the split DFT-16 fragment tables of the tensor-core passes (gbd_tc.cuh) into the
+// GBD_TC_FRAG_F2 float2 slots at frag (the mesh's twiddle buffer after its levels).
+void launch_dft16_frags(float2* frag, cudaStream_t st);
 bool launch_film_conv(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st);
 bool launch_y_fwd(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st);
 bool launch_y_inv(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st);

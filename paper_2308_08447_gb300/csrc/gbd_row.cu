@@ -113,6 +113,30 @@ bool launch_row(int Lx, int var, int prec, const RowArgs& a0, const float2* tw, 
   return row_dispatch(Lx, var, prec, &a, tw, st);
 }
 
+// One warp: lane l writes register r of each table at word r * 32 + l (Dft16Frags::load).
+__global__ void __launch_bounds__(32) dft16_frag_kernel(unsigned* frag) {
+  const int lane = threadIdx.x & 31;
+  auto put = [&](const unsigned* f, int table) {
+    for (int r = 0; r < 32; ++r) frag[table * 1024 + r * 32 + lane] = f[r];
+  };
+  Dft16Frags<-1, 1> a;
+  a.build(lane);
+  put(&a.f[0][0][0][0], 0);
+  Dft16Frags<1, 1> b;
+  b.build(lane);
+  put(&b.f[0][0][0][0], 1);
+  Dft16Frags<-1, 2> c;
+  c.build(lane);
+  put(&c.f[0][0][0][0], 2);
+  Dft16Frags<1, 2> d;
+  d.build(lane);
+  put(&d.f[0][0][0][0], 3);
+}
+
+void launch_dft16_frags(float2* frag, cudaStream_t st) {
+  dft16_frag_kernel<<<1, 32, 0, st>>>(reinterpret_cast<unsigned*>(frag));
+}
+
 void launch_rkf_final(const RkfArgs& a, cudaStream_t st) {
   rkf_final_kernel<<<(unsigned)((a.N + 255) / 256), 256, 0, st>>>(a);
 }

@@ -116,6 +116,13 @@ struct Dft16Frags {
         for (int i = 0; i < 4; ++i) split2<PREC>(v[2 * i], v[2 * i + 1], f[mt][kt][0][i], f[mt][kt][1][i]);
       }
   }
+  // The same fragments from the table that dft16_frag_kernel wrote once per mesh after the
+  // twiddle levels: register r of lane l at word r * 32 + l of table (PREC - 1) * 2 + (S > 0).
+  __device__ __forceinline__ void load(const float2* __restrict__ tw, int lane) {
+    const unsigned* F = reinterpret_cast<const unsigned*>(tw + 2 * GBD_TW_LEN) + ((PREC - 1) * 2 + (S > 0)) * 1024;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) (&f[0][0][0][0])[r] = __ldg(F + r * 32 + lane);
+  }
 };
 
 // Radix-16 pass (forward: loads j + r L/16, stores (j-k) 16 + k + q Ns; adjoint: reverse),
@@ -155,7 +162,7 @@ __device__ __forceinline__ void stockham_pass_tc(const float2* __restrict__ tw, 
   }
   if (SYNC_MID) __syncthreads();
   Dft16Frags<S, PREC> A;
-  A.build(lane);
+  A.load(tw, lane);
 #pragma unroll
   for (int grp = 0; grp < 4; ++grp) {
     // FP16: butterfly g's inputs sit on lanes 4g .. 4g+3; scale them by 2^-e, e the binary

@@ -65,7 +65,7 @@ def test_mesh_bytes_counts_buffers(g):
     S = 3 * 1025 * 1024 * 8
     K = 1025 * 1025 * 16
     state = 9 * N * 4
-    twiddles = 2 * 8192 * 8   # all power-of-two levels up to 8192 entries
+    twiddles = 2 * 8192 * 8 + 4 * 32 * 32 * 4   # power-of-two levels up to 8192; split DFT-16 fragments
     assert b == S + K + state + twiddles
 
 
