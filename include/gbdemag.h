@@ -79,7 +79,7 @@ typedef struct {
  * offset the +n_d/2 and -n_d/2 image sets are averaged, so every component keeps its parity),
  * and the exchange Laplacian wraps around. Images beyond 256 cell sizes enter as point dipoles.
  * The kernel set-up costs about octant * (2 pbc_images + 1)^(periodic axes) tensor terms on
- * the host. gbd_set_kernel_tensor is not available for periodic meshes (GBD_EUNSUPPORTED). */
+ * the host. gbd_set_kernel_tensor takes a caller tensor on one period along periodic axes. */
 #define GBD_FLAG_PBC_X 1u
 #define GBD_FLAG_PBC_Y 2u
 #define GBD_FLAG_PBC_Z 4u
@@ -108,13 +108,15 @@ gbd_status gbd_set_kernel(gbd_mesh* mesh, void* stream);
 
 /* Like gbd_set_kernel, but with the caller's FP64 tensor instead of the built-in one (Eq. 1
  * holds for any interaction tensor with the demag tensor's symmetries, e.g. one summed over
- * periodic images or a dipole-dipole kernel). N6: host array [6][2nz-1][2ny-1][2nx-1] of
- * (xx, yy, zz, xy, xz, yz), element (X, Y, Z) at index ((c (2nz-1) + Z+nz-1) (2ny-1) + Y+ny-1)
- * (2nx-1) + X+nx-1, for offsets |X| < nx, |Y| < ny, |Z| < nz; read only during the call.
+ * periodic images or a dipole-dipole kernel). N6: host array [6][Gz][Gy][Gx] of
+ * (xx, yy, zz, xy, xz, yz), element (X, Y, Z) at index ((c Gz + gz(Z)) Gy + gy(Y)) Gx + gx(X);
+ * read only during the call. Along an open axis of n cells G = 2n - 1 and g(X) = X + n - 1 for
+ * offsets |X| < n. Along a periodic axis (GBD_FLAG_PBC_*) G = n and g(X) = X mod n: one period
+ * of the (image-summed) tensor, for offsets 0 .. n - 1 (equivalently -n/2 < X <= n/2).
  * Each component must be finite and have the parities of the demag tensor (xx, yy, zz even in
- * X, Y, Z; xy odd in X and Y; xz odd in X and Z; yz odd in Y and Z), to within
- * GBD_TENSOR_SYM_TOL times the largest magnitude in N6; otherwise GBD_EINVAL and nothing
- * changes.
+ * X, Y, Z; xy odd in X and Y; xz odd in X and Z; yz odd in Y and Z; on a period the mirror of
+ * X is n - X, so an odd component vanishes at X = n/2), to within GBD_TENSOR_SYM_TOL times the
+ * largest magnitude in N6; otherwise GBD_EINVAL and nothing changes.
  * Only the octant X, Y, Z >= 0 is then used. The result is not put into the host cache.
  * Blocks until the copy is done. */
 #define GBD_TENSOR_SYM_TOL 1e-9

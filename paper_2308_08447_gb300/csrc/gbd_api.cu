@@ -601,10 +601,9 @@ gbd_status gbd_set_kernel(gbd_mesh* m, void* stream) {
   return upload_spectrum(m, spec, st, &key);
 }
 
-// Spectrum of a caller tensor [6][2nz-1][2ny-1][2nx-1] (see gbd_set_kernel_tensor).
+// Spectrum of a caller tensor [6][Gz][Gy][Gx] (see gbd_set_kernel_tensor).
 static gbd_status spectrum_of_tensor(const gbd::Plan& p, const double* N6, std::vector<double>& spec) {
   if (!N6) return fail(GBD_EINVAL, "tensor is NULL");
-  if (p.per) return fail(GBD_EUNSUPPORTED, "caller tensors are not available for periodic meshes");
   std::vector<double> oct;
   const int r = gbdt::octant_from_full(p, N6, oct, GBD_TENSOR_SYM_TOL);
   if (r < 0) return fail(GBD_ENOMEM, "host allocation failed");

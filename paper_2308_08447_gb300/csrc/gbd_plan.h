@@ -51,8 +51,9 @@ void tensor_at(int X, int Y, int Z, double dx, double dy, double dz, double out[
 bool kernel_spectrum(const gbd::Plan& p, double dx, double dy, double dz, std::vector<double>& out);
 // Packed spectrum from the octant X, Y, Z >= 0 of the six components, layout [6][nz][ny][nx].
 bool spectrum_from_octant(const gbd::Plan& p, const std::vector<double>& oct, std::vector<double>& out);
-// Octant of a caller tensor [6][2nz-1][2ny-1][2nx-1] after checking that the values are finite
-// and have the tensor's parities within tol times the largest magnitude of all components.
+// Octant of a caller tensor [6][Gz][Gy][Gx] (G_d = 2 n_d - 1 on an open axis, n_d on a periodic
+// one) after checking that the values are finite and have the tensor's parities within tol times
+// the largest magnitude of all components.
 // Returns 0, 1 (not finite or not symmetric) or -1 (allocation failure).
 int octant_from_full(const gbd::Plan& p, const double* full, std::vector<double>& oct, double tol);
 }  // namespace gbdt

@@ -311,44 +311,62 @@ bool kernel_spectrum(const gbd::Plan& p, double dx, double dy, double dz, std::v
   return spectrum_from_octant(p, oct, out);
 }
 
-// Index of offset (X, Y, Z) in a caller tensor laid out [6][2nz-1][2ny-1][2nx-1].
-static inline size_t full_index(const gbd::Plan& p, int c, int X, int Y, int Z) {
-  const size_t wx = 2 * (size_t)p.nx - 1, wy = 2 * (size_t)p.ny - 1, wz = 2 * (size_t)p.nz - 1;
-  return (((size_t)c * wz + (size_t)(Z + p.nz - 1)) * wy + (size_t)(Y + p.ny - 1)) * wx + (size_t)(X + p.nx - 1);
-}
+// Grid of a caller tensor along one axis: an open axis of n cells holds the offsets 1-n .. n-1
+// at index X + n - 1 (2n - 1 entries); a periodic axis holds one period, offset X at index
+// X mod n (n entries; the offsets taken as b for b <= n/2 and b - n above).
+struct AxisGrid {
+  int n = 1;
+  bool per = false;
+  int size() const { return per ? n : 2 * n - 1; }
+  int index(int X) const { return per ? ((X % n) + n) % n : X + n - 1; }
+  int offset(int g) const { return per ? (2 * g <= n ? g : g - n) : g - (n - 1); }
+};
 
 int octant_from_full(const gbd::Plan& p, const double* full, std::vector<double>& oct, double tol) {
-  const int nx = p.nx, ny = p.ny, nz = p.nz;
-  const long long Noct = (long long)nx * ny * nz;
+  AxisGrid gx, gy, gz;
+  gx.n = p.nx;
+  gx.per = (p.per & 1) != 0;
+  gy.n = p.ny;
+  gy.per = (p.per & 2) != 0;
+  gz.n = p.nz;
+  gz.per = (p.per & 4) != 0;
+  const size_t Gx = gx.size(), Gy = gy.size(), Gz = gz.size();
+  auto at = [&](int c, int X, int Y, int Z) {
+    return full[(((size_t)c * Gz + (size_t)gz.index(Z)) * Gy + (size_t)gy.index(Y)) * Gx + (size_t)gx.index(X)];
+  };
+  const int ox = p.ox, oy = p.oy, oz = p.oz;
+  const long long Noct = (long long)ox * oy * oz;
   try {
     oct.resize((size_t)Noct * 6);
   } catch (...) {
     return -1;
   }
+  const size_t total = (size_t)6 * Gz * Gy * Gx;
   double mx = 0.0;
-  for (int c = 0; c < 6; ++c)
-    for (int Z = 1 - nz; Z < nz; ++Z)
-      for (int Y = 1 - ny; Y < ny; ++Y)
-        for (int X = 1 - nx; X < nx; ++X) mx = std::fmax(mx, std::fabs(full[full_index(p, c, X, Y, Z)]));
+  for (size_t i = 0; i < total; ++i) {
+    if (!std::isfinite(full[i])) return 1;
+    mx = std::fmax(mx, std::fabs(full[i]));
+  }
   const double lim = tol * mx;
   for (int c = 0; c < 6; ++c) {
-    for (int Z = 1 - nz; Z < nz; ++Z)
-      for (int Y = 1 - ny; Y < ny; ++Y)
-        for (int X = 1 - nx; X < nx; ++X) {
-          const double v = full[full_index(p, c, X, Y, Z)];
-          if (!std::isfinite(v)) return 1;
+    for (size_t kz = 0; kz < Gz; ++kz)
+      for (size_t ky = 0; ky < Gy; ++ky)
+        for (size_t kx = 0; kx < Gx; ++kx) {
+          const int X = gx.offset((int)kx), Y = gy.offset((int)ky), Z = gz.offset((int)kz);
+          const double v = at(c, X, Y, Z);
+          // the value at the mirrored offset, signed by the component's parities
           const double sgn = (X < 0 ? PARITY[c][0] : 1) * (Y < 0 ? PARITY[c][1] : 1) * (Z < 0 ? PARITY[c][2] : 1);
-          const double ref = sgn * full[full_index(p, c, std::abs(X), std::abs(Y), std::abs(Z))];
-          if (std::fabs(v - ref) > lim) return 1;
-          // an odd component is zero on its odd axis planes
-          if (((PARITY[c][0] < 0 && X == 0) || (PARITY[c][1] < 0 && Y == 0) || (PARITY[c][2] < 0 && Z == 0)) &&
+          if (std::fabs(v - sgn * at(c, std::abs(X), std::abs(Y), std::abs(Z))) > lim) return 1;
+          // an odd component vanishes where its offset is its own mirror (0, or n/2 on a period)
+          auto self_mirror = [](const AxisGrid& g, int O) { return O == 0 || (g.per && 2 * O == g.n); };
+          if (((PARITY[c][0] < 0 && self_mirror(gx, X)) || (PARITY[c][1] < 0 && self_mirror(gy, Y)) ||
+               (PARITY[c][2] < 0 && self_mirror(gz, Z))) &&
               std::fabs(v) > lim)
             return 1;
         }
-    for (int Z = 0; Z < nz; ++Z)
-      for (int Y = 0; Y < ny; ++Y)
-        for (int X = 0; X < nx; ++X)
-          oct[(size_t)c * Noct + ((size_t)Z * ny + Y) * nx + X] = full[full_index(p, c, X, Y, Z)];
+    for (int Z = 0; Z < oz; ++Z)
+      for (int Y = 0; Y < oy; ++Y)
+        for (int X = 0; X < ox; ++X) oct[(size_t)c * Noct + ((size_t)Z * oy + Y) * ox + X] = at(c, X, Y, Z);
   }
   return 0;
 }

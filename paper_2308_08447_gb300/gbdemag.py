@@ -157,19 +157,20 @@ def gbd_set_kernel(mesh, stream=None):
     _check(load().gbd_set_kernel(mesh, _stream_ptr(stream)))
 
 
-def _tensor_arg(N6, n):
-    """C-contiguous float64 copy of a caller tensor of shape (6, 2nz-1, 2ny-1, 2nx-1)."""
+def _tensor_arg(N6, n, pbc=(False,) * 3):
+    """C-contiguous float64 copy of a caller tensor of shape (6, Gz, Gy, Gx): G = 2n - 1 along an
+    open axis, n along a periodic one."""
     import numpy as np
-    nx, ny, nz = n
-    want = (6, 2 * nz - 1, 2 * ny - 1, 2 * nx - 1)
+    G = [n[d] if pbc[d] else 2 * n[d] - 1 for d in range(3)]
+    want = (6, G[2], G[1], G[0])
     arr = np.ascontiguousarray(N6, dtype=np.float64)
     if arr.shape != want:
         raise ValueError("tensor shape %s != %s" % (arr.shape, want))
     return arr
 
 
-def gbd_set_kernel_tensor(mesh, N6, n, stream=None):
-    arr = _tensor_arg(N6, n)
+def gbd_set_kernel_tensor(mesh, N6, n, stream=None, pbc=(False,) * 3):
+    arr = _tensor_arg(N6, n, pbc)
     _check(load().gbd_set_kernel_tensor(mesh, arr.ctypes.data_as(ctypes.POINTER(_D)), _stream_ptr(stream)))
 
 
@@ -313,7 +314,7 @@ def gbd_kernel_spectrum_host(desc):
 def gbd_kernel_spectrum_from_tensor_host(desc, N6):
     import numpy as np
     Px, Py, Pz, Hx, Ky, Kz = gbd_plan_dims(desc)
-    arr = _tensor_arg(N6, (desc.nx, desc.ny, desc.nz))
+    arr = _tensor_arg(N6, (desc.nx, desc.ny, desc.nz), tuple(bool(desc.flags >> d & 1) for d in range(3)))
     out = np.zeros((6, Kz, Ky, Hx), dtype=np.float64)
     _check(load().gbd_kernel_spectrum_from_tensor_host(ctypes.byref(desc), arr.ctypes.data_as(ctypes.POINTER(_D)),
                                                        out.ctypes.data_as(ctypes.POINTER(_D)), out.size))
@@ -328,6 +329,7 @@ class Mesh:
     def __init__(self, n, cell, Ms, A_ex=0.0, alpha=0.0, gamma=0.0, Hext=(0.0, 0.0, 0.0),
                  precision=GBD_FP32, set_kernel=True, stream=None, pbc=(False,) * 3, pbc_images=0):
         self.n = tuple(int(v) for v in n)
+        self.pbc = tuple(bool(v) for v in pbc)
         self.shape = (3, self.n[2], self.n[1], self.n[0])
         self.desc = make_desc(n, cell, Ms, A_ex, alpha, gamma, Hext, precision, pbc, pbc_images)
         self.handle = gbd_mesh_create(self.desc)
@@ -335,8 +337,9 @@ class Mesh:
             gbd_set_kernel(self.handle, stream)
 
     def set_kernel_tensor(self, N6, stream=None):
-        """Replace the kernel by the caller's FP64 tensor, shape (6, 2nz-1, 2ny-1, 2nx-1)."""
-        gbd_set_kernel_tensor(self.handle, N6, self.n, stream)
+        """Replace the kernel by the caller's FP64 tensor, shape (6, Gz, Gy, Gx) with G = 2n - 1
+        along open axes and n (one period, offset X at index X mod n) along periodic ones."""
+        gbd_set_kernel_tensor(self.handle, N6, self.n, stream, self.pbc)
 
     def demag(self, M, H, stream=None):
         gbd_demag(self.handle, M, H, self.shape, stream)

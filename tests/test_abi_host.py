@@ -236,10 +236,60 @@ def test_periodic_desc_checks(g):
         with pytest.raises(g.GbdError) as ei:      # no length-2 y or z transforms
             g.gbd_plan_dims(g.make_desc(n, cell, 8e5, pbc=pbc, pbc_images=2))
         assert ei.value.status == g.GBD_EUNSUPPORTED
-    with pytest.raises(g.GbdError) as ei:          # caller tensors are for open boundaries
-        g.gbd_kernel_spectrum_from_tensor_host(g.make_desc((4, 4, 1), cell, 8e5, pbc=(True, True, False),
-                                                           pbc_images=1), np.zeros((6, 1, 7, 7)))
-    assert ei.value.status == g.GBD_EUNSUPPORTED
+
+
+def _periodic_fft_spectrum(Kg, n, pbc, dims):
+    """numpy FFT of a tensor on the convolution grid (one period along periodic axes, offsets
+    1-n .. n-1 along the others), placed on the padded lengths, packed and scaled."""
+    Px, Py, Pz, Hx, Ky, Kz = dims
+    P = (Px, Py, Pz)
+    Kp = np.zeros((6, Pz, Py, Px))
+    idx = [np.arange(Kg.shape[3 - d]) if pbc[d] else (np.arange(Kg.shape[3 - d]) - (n[d] - 1)) % P[d] for d in range(3)]
+    for c in range(6):
+        Kp[c][np.ix_(idx[2], idx[1], idx[0])] = Kg[c]
+    Kh = np.fft.fftn(Kp, axes=(1, 2, 3))
+    want = -Kh.real[:, :Kz, :Ky, :Hx] / (Px * Py * Pz)
+    if n[2] == 1:
+        want[4:] = 0.0
+    return want
+
+
+@pytest.mark.parametrize("n,pbc,images", [((16, 8, 1), (True, True, False), 2), ((16, 12, 4), (True, False, False), 1),
+                                          ((8, 8, 4), (False, False, True), 1), ((4, 8, 4), (True, True, True), 1)])
+def test_periodic_caller_tensor_spectrum(g, n, pbc, images):
+    # one period of the oracle's image-summed tensor through the caller path equals numpy's FFT of
+    # it, and the built-in periodic spectrum to the two image sums' agreement
+    from oracle import pbc as B
+    cell = (2e-9, 3e-9, 2.5e-9)
+    desc = g.make_desc(n, cell, 8e5, pbc=pbc, pbc_images=images)
+    dims = g.gbd_plan_dims(desc)
+    Kg = B.periodic_kernel(n, cell, pbc, images)
+    spec = g.gbd_kernel_spectrum_from_tensor_host(desc, Kg)
+    want = _periodic_fft_spectrum(Kg, n, pbc, dims)
+    assert np.abs(spec - want).max() <= 1e-12 * np.abs(want).max()
+    assert np.abs(spec - g.gbd_kernel_spectrum_host(desc)).max() <= 1e-8 * np.abs(want).max()
+
+
+def test_periodic_caller_tensor_checks(g):
+    from oracle import pbc as B
+    n, pbc, cell = (8, 4, 1), (True, False, False), (2e-9, 2e-9, 3e-9)
+    desc = g.make_desc(n, cell, 8e5, pbc=pbc, pbc_images=1)
+    Kg = B.periodic_kernel(n, cell, pbc, 1)
+    assert Kg.shape == (6, 1, 7, 8)
+    g.gbd_kernel_spectrum_from_tensor_host(desc, Kg)
+    bad = Kg.copy()
+    bad[3, 0, 4, 4] += 1e-3 * np.abs(Kg).max()         # xy is odd in X: it vanishes at X = n/2
+    bad[3, 0, 2, 4] -= 1e-3 * np.abs(Kg).max()
+    with pytest.raises(g.GbdError) as ei:
+        g.gbd_kernel_spectrum_from_tensor_host(desc, bad)
+    assert ei.value.status == g.GBD_EINVAL
+    bad = Kg.copy()
+    bad[0, 0, 3, 1] += 1e-3 * np.abs(Kg).max()         # xx at X = 1 without its mirror X = 7
+    with pytest.raises(g.GbdError) as ei:
+        g.gbd_kernel_spectrum_from_tensor_host(desc, bad)
+    assert ei.value.status == g.GBD_EINVAL
+    with pytest.raises(ValueError):                    # open-boundary shape on a periodic axis
+        g.gbd_kernel_spectrum_from_tensor_host(desc, np.zeros((6, 1, 7, 15)))
 
 
 def test_precision_values(g):

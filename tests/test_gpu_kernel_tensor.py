@@ -2,7 +2,8 @@
 
 With the oracle's tensor the field matches the oracle's FFT convolution and the built-in
 kernel's field; with a tensor that is only a self term the field is local, H_i = -N(0) M_i;
-a tensor without the demag parities is refused and leaves the previous kernel in place.
+a tensor without the demag parities is refused and leaves the previous kernel in place; on a
+periodic mesh one period of an image-summed tensor gives the circular convolution.
 """
 import numpy as np
 import pytest
@@ -71,3 +72,22 @@ def test_asymmetric_tensor_refused_kernel_kept(g):
     mesh.demag(M, H1)
     assert torch.equal(H0, H1)
     mesh.close()
+
+
+@pytest.mark.parametrize("n,cell,pbc", [((32, 16, 1), (2e-9, 2e-9, 3e-9), (True, True, False)),
+                                        ((16, 12, 4), (3e-9, 3e-9, 3e-9), (False, False, True))])
+def test_periodic_caller_tensor(g, n, cell, pbc):
+    # one period of the oracle's image-summed tensor, set by the caller on a periodic mesh, gives
+    # the oracle's circular convolution (the reading of the periodic kernel in oracle/pbc.py)
+    import torch
+    from oracle import pbc as B
+    Ms = 8e5
+    Kg = B.periodic_kernel(n, cell, pbc, 1)
+    M = (Ms * W.random_unit(n, 13)).astype(np.float32)
+    mesh = g.Mesh(n, cell, Ms, pbc=pbc, pbc_images=1, set_kernel=False)
+    mesh.set_kernel_tensor(Kg)
+    H = torch.empty(M.shape, device="cuda")
+    mesh.demag(to_dev(M), H)
+    h = to_host(H)
+    mesh.close()
+    assert e_inf(h, B.conv_periodic(M.astype(np.float64), Kg, pbc)) <= TOL_FP32
