@@ -90,7 +90,9 @@ typedef struct gbd_mesh gbd_mesh; /* opaque: plan, kernel spectrum, scratch, RK4
  * periodic axis) and
  * allocates the mesh's device buffers on the current device: x spectrum, 3D y spectrum,
  * kernel spectrum, RK4 scratch, twiddle table. *out receives the mesh (NULL on failure).
- * Errors: GBD_EINVAL, GBD_EUNSUPPORTED, GBD_ENOMEM, GBD_ECUDA. */
+ * Errors: GBD_EINVAL, GBD_EUNSUPPORTED, GBD_ENOMEM, GBD_ECUDA. On any error every buffer
+ * allocated so far is freed. Test hook: with the environment variable GBD_TEST_FAIL_ALLOC=k
+ * (read at each call) the k-th of these device allocations fails as out-of-memory. */
 gbd_status gbd_mesh_create(const gbd_mesh_desc* desc, gbd_mesh** out);
 
 /* Device bytes gbd_mesh_create would allocate for desc (for admission control). Host only. */

@@ -386,9 +386,14 @@ gbd_status gbd_mesh_create(const gbd_mesh_desc* desc, gbd_mesh** out) {
                 {(void**)&m->K, p.bytes_K},      {(void**)&m->acc, p.bytes_state / 3},
                 {(void**)&m->bufA, p.bytes_state / 3}, {(void**)&m->bufB, p.bytes_state / 3},
                 {(void**)&m->tw, p.bytes_tw}};
+  // test hook: GBD_TEST_FAIL_ALLOC=k makes the k-th device allocation below report
+  // out-of-memory without calling cudaMalloc (exercises the clean-up path)
+  const char* fail_env = std::getenv("GBD_TEST_FAIL_ALLOC");
+  const int fail_at = fail_env ? std::atoi(fail_env) : 0;
+  int nalloc = 0;
   for (auto& al : allocs) {
     if (al.bytes == 0) continue;
-    e = cudaMalloc(al.ptr, al.bytes);
+    e = (++nalloc == fail_at) ? cudaErrorMemoryAllocation : cudaMalloc(al.ptr, al.bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
       free_mesh_buffers(m);
