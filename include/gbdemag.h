@@ -184,6 +184,21 @@ gbd_status gbd_llg_step_ex(gbd_mesh* mesh, float* m, int nsteps, double dt, unsi
  * re-captures its graph on its next run. GBD_EINVAL for non-finite values. */
 gbd_status gbd_mesh_set_params(gbd_mesh* mesh, const double Hext[3], double alpha);
 
+/* Checkpoint / resume of the integrator state that lives in the mesh (no counterpart in the
+ * paper): the demag-extrapolation histories of gbd_llg_step_ex (GBD_STEP_EXTRAP) and of the
+ * RKF5(6) calls, with their ring positions and step times. m itself is the caller's array.
+ * gbd_mesh_state_bytes gives the size of the host image (a header plus 5 resp. 6 slots of
+ * [3][nz][ny][nx] float32 for each history the mesh has allocated). gbd_mesh_get_state waits
+ * for stream, then copies the state into host (bytes >= that size, else GBD_EINVAL).
+ * gbd_mesh_set_state waits for stream and replaces the mesh's state by an image from a mesh
+ * with the same number of cells (GBD_EINVAL for a malformed or foreign image, which changes
+ * nothing); a following call with GBD_STEP_CONTINUE resumes exactly where the saved mesh
+ * stood, so a run split by get/set (even across processes) equals the unsplit run bit for
+ * bit. Both block the host. */
+gbd_status gbd_mesh_state_bytes(const gbd_mesh* mesh, size_t* out);
+gbd_status gbd_mesh_get_state(gbd_mesh* mesh, void* host, size_t bytes, void* stream);
+gbd_status gbd_mesh_set_state(gbd_mesh* mesh, const void* host, size_t bytes, void* stream);
+
 /* ---- allocation-free demag --------------------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that cannot call
  * cudaMalloc at the moment they need the field -- for example code embedded in a host

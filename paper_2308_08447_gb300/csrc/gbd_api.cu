@@ -1015,6 +1015,103 @@ gbd_status gbd_llg_step(gbd_mesh* m, float* mm, int nsteps, double dt, void* str
   return gbd_llg_step_ex(m, mm, nsteps, dt, 0u, stream);
 }
 
+// ---- integrator state (checkpoint / resume) ---------------------------------------------------
+// Host image: a fixed header, then the RK4 demag history (5 slots of [3][N] float32) if the
+// mesh has one, then the RKF5(6) history (6 slots) if it has one.
+struct StateHeader {
+  char magic[8];            // "GBDSTAT1"
+  long long N;              // cells
+  int has_hist, hist_count, hist_head, has_rk;
+  double hist_dt;
+  int rk_ring[5];
+  int rk_count, rk_pend;
+  double rk_ring_t[5];
+};
+static const char kStateMagic[8] = {'G', 'B', 'D', 'S', 'T', 'A', 'T', '1'};
+
+static size_t state_bytes(const gbd_mesh* m) {
+  const size_t slot = (size_t)3 * m->p.N * sizeof(float);
+  return sizeof(StateHeader) + (m->hist ? 5 * slot : 0) + (m->rk_hist ? 6 * slot : 0);
+}
+
+gbd_status gbd_mesh_state_bytes(const gbd_mesh* m, size_t* out) {
+  if (!m || !out) return fail(GBD_EINVAL, "mesh or out is NULL");
+  *out = state_bytes(m);
+  return GBD_OK;
+}
+
+gbd_status gbd_mesh_get_state(gbd_mesh* m, void* host, size_t bytes, void* stream) {
+  if (!m || !host) return fail(GBD_EINVAL, "mesh or buffer is NULL");
+  gbd_status s = check_device(m);
+  if (s != GBD_OK) return s;
+  if (bytes < state_bytes(m)) return fail(GBD_EINVAL, "buffer smaller than gbd_mesh_state_bytes");
+  StateHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, kStateMagic, sizeof(kStateMagic));
+  h.N = m->p.N;
+  h.has_hist = m->hist != nullptr;
+  h.hist_count = m->hist_count;
+  h.hist_head = m->hist_head;
+  h.hist_dt = m->hist_dt;
+  h.has_rk = m->rk_hist != nullptr;
+  for (int i = 0; i < 5; ++i) {
+    h.rk_ring[i] = m->rk_ring[i];
+    h.rk_ring_t[i] = m->rk_ring_t[i];
+  }
+  h.rk_count = m->rk_count;
+  h.rk_pend = m->rk_pend;
+  char* out = static_cast<char*>(host);
+  std::memcpy(out, &h, sizeof(h));
+  out += sizeof(h);
+  const size_t slot = (size_t)3 * m->p.N * sizeof(float);
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess && m->hist) {
+    e = cudaMemcpy(out, m->hist, 5 * slot, cudaMemcpyDeviceToHost);
+    out += 5 * slot;
+  }
+  if (e == cudaSuccess && m->rk_hist) e = cudaMemcpy(out, m->rk_hist, 6 * slot, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "gbd_mesh_get_state");
+  return GBD_OK;
+}
+
+gbd_status gbd_mesh_set_state(gbd_mesh* m, const void* host, size_t bytes, void* stream) {
+  if (!m || !host) return fail(GBD_EINVAL, "mesh or buffer is NULL");
+  gbd_status s = check_device(m);
+  if (s != GBD_OK) return s;
+  StateHeader h;
+  if (bytes < sizeof(h)) return fail(GBD_EINVAL, "buffer shorter than a state header");
+  std::memcpy(&h, host, sizeof(h));
+  const size_t slot = (size_t)3 * m->p.N * sizeof(float);
+  const bool ring_ok = h.rk_count >= 0 && h.rk_count <= 5 && h.rk_pend >= 0 && h.rk_pend < 6 &&
+                       std::all_of(h.rk_ring, h.rk_ring + 5, [](int v) { return v >= 0 && v < 6; });
+  if (std::memcmp(h.magic, kStateMagic, sizeof(kStateMagic)) != 0 || h.N != m->p.N || h.hist_count < 0 ||
+      h.hist_count > 5 || h.hist_head < 0 || h.hist_head >= 5 || !ring_ok)
+    return fail(GBD_EINVAL, "not a state image of a mesh with this many cells");
+  if (bytes != sizeof(h) + (h.has_hist ? 5 * slot : 0) + (h.has_rk ? 6 * slot : 0))
+    return fail(GBD_EINVAL, "state image size does not match its header");
+  if (h.has_hist && (s = ensure_history(m)) != GBD_OK) return s;
+  if (h.has_rk && (s = ensure_rkf_history(m)) != GBD_OK) return s;
+  const char* in = static_cast<const char*>(host) + sizeof(h);
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess && h.has_hist) {
+    e = cudaMemcpy(m->hist, in, 5 * slot, cudaMemcpyHostToDevice);
+    in += 5 * slot;
+  }
+  if (e == cudaSuccess && h.has_rk) e = cudaMemcpy(m->rk_hist, in, 6 * slot, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "gbd_mesh_set_state");
+  m->hist_count = h.has_hist ? h.hist_count : 0;
+  m->hist_head = h.hist_head;
+  m->hist_dt = h.hist_dt;
+  for (int i = 0; i < 5; ++i) {
+    m->rk_ring[i] = h.rk_ring[i];
+    m->rk_ring_t[i] = h.rk_ring_t[i];
+  }
+  m->rk_count = h.has_rk ? h.rk_count : 0;
+  m->rk_pend = h.rk_pend;
+  ++m->version;   // batch graphs keyed on the history state re-capture
+  return GBD_OK;
+}
+
 }  // extern "C"
 
 // ---- allocation-free demag -------------------------------------------------------------------

@@ -50,6 +50,9 @@ _SIG = {
     "gbd_llg_step": [_P, _P, _I, _D, _P],
     "gbd_llg_step_ex": [_P, _P, _I, _D, ctypes.c_uint, _P],
     "gbd_mesh_set_params": [_P, ctypes.POINTER(_D), _D],
+    "gbd_mesh_state_bytes": [_P, ctypes.POINTER(ctypes.c_size_t)],
+    "gbd_mesh_get_state": [_P, _P, ctypes.c_size_t, _P],
+    "gbd_mesh_set_state": [_P, _P, ctypes.c_size_t, _P],
     "gbd_llg_rkf56_step": [_P, _P, _D, ctypes.POINTER(_D), ctypes.c_uint, _P],
     "gbd_llg_run_rkf56": [_P, _P, _D, ctypes.POINTER(_D), _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.c_uint,
                           _P],
@@ -215,6 +218,20 @@ def gbd_mesh_set_params(mesh, Hext=None, alpha=None):
     _check(load().gbd_mesh_set_params(mesh, h, -1.0 if alpha is None else float(alpha)))
 
 
+def gbd_mesh_get_state(mesh, stream=None):
+    """The mesh's integrator state (extrapolation histories) as bytes (gbd_mesh_get_state)."""
+    n = ctypes.c_size_t()
+    _check(load().gbd_mesh_state_bytes(mesh, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(load().gbd_mesh_get_state(mesh, ctypes.cast(buf, _P), n.value, _stream_ptr(stream)))
+    return buf.raw
+
+
+def gbd_mesh_set_state(mesh, state, stream=None):
+    buf = ctypes.create_string_buffer(bytes(state), len(state))
+    _check(load().gbd_mesh_set_state(mesh, ctypes.cast(buf, _P), len(state), _stream_ptr(stream)))
+
+
 def gbd_llg_rkf56_step(mesh, m, dt, shape, stream=None, flags=0):
     """One RKF5(6) step; returns the error estimate."""
     err = _D(0.0)
@@ -367,6 +384,14 @@ class Mesh:
         """Adaptive RKF5(6) over [0, t_end]; returns (next dt, accepted, rejected)."""
         flags = (GBD_STEP_EXTRAP if extrap else 0) | (GBD_STEP_CONTINUE if cont else 0)
         return gbd_llg_run_rkf56(self.handle, m, t_end, dt, tol, self.shape, max_steps, stream, flags)
+
+    def get_state(self, stream=None):
+        """Checkpoint of the integrator state kept in the mesh (bytes); m is the caller's."""
+        return gbd_mesh_get_state(self.handle, stream)
+
+    def set_state(self, state, stream=None):
+        """Resume from get_state's bytes (a mesh with the same cell count); continue with cont=True."""
+        gbd_mesh_set_state(self.handle, state, stream)
 
     def set_params(self, Hext=None, alpha=None):
         """Applied field (A/m) and/or damping of later calls (None keeps the current value)."""
