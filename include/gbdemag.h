@@ -25,8 +25,8 @@
  *     gbd_last_error() gives a message (per calling thread). Argument errors are detected
  *     before any work is enqueued. A CUDA error raised by enqueued work surfaces as
  *     GBD_ECUDA from a later call on the same device (CUDA errors are sticky).
- *   - Boundaries are free: no periodic images, and the exchange Laplacian replaces a
- *     missing neighbour by the cell itself (Neumann).
+ *   - Boundaries are free unless an axis is made periodic (GBD_FLAG_PBC_*): the exchange
+ *     Laplacian replaces a missing neighbour by the cell itself (Neumann).
  */
 #ifndef GBDEMAG_H
 #define GBDEMAG_H
@@ -290,8 +290,15 @@ enum {
   GBD_NPASS = 8
 };
 
-/* enable != 0: every later launch of this mesh is bracketed by two CUDA events on its
- * stream (profiling only; it adds event records between launches). */
+/* Tracing of this mesh's later launches (profiling only). enable = 0: off. GBD_TIMING_EVENTS
+ * (also any other nonzero value without the NVTX bit): every launch is bracketed by two CUDA
+ * events on its stream (it adds event records between launches), read by
+ * gbd_mesh_read_timing. GBD_TIMING_NVTX: every launch's enqueue is wrapped in an NVTX range
+ * named after its pass class ("row_fwd", "row_inv", "row_rk", "film_conv", "y_fwd", "z_conv",
+ * "y_inv", "extrap_stage"), for profilers that filter kernels by NVTX range; the two combine.
+ * Batched runs (gbd_batch_run*) are not traced. */
+#define GBD_TIMING_EVENTS 1
+#define GBD_TIMING_NVTX 2
 gbd_status gbd_mesh_set_timing(gbd_mesh* mesh, int enable);
 
 /* Waits for the recorded events, writes per pass class the summed device time in ms and

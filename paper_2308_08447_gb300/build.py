@@ -83,7 +83,7 @@ def build(verbose=False, ptxas_info=False):
                 print(log)
     objs = [os.path.join(BUILD, u + ".o") for u in CUDA_UNITS + CXX_UNITS]
     if jobs or not os.path.exists(LIB):
-        _run([nvcc, "-shared", *ARCH, "-o", LIB, *objs, "-Xcompiler", "-fopenmp", "-lgomp", "-lcudart"])
+        _run([nvcc, "-shared", *ARCH, "-o", LIB, *objs, "-Xcompiler", "-fopenmp", "-lgomp", "-lcudart", "-ldl"])
     return LIB
 
 

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "gbdemag.h"
 #include "gbd_fft.cuh"
@@ -65,19 +66,18 @@ struct gbd_mesh {
   int rk_count = 0, rk_pend = 5;
   bool kernel_set = false;
   // optional per-launch timing: events[2i], events[2i+1] bracket launch i of class cls[i]
-  bool timing = false;
+  int timing = 0;           // GBD_TIMING_EVENTS | GBD_TIMING_NVTX
   std::vector<cudaEvent_t> events;
   std::vector<int> cls;
   size_t used = 0;
 };
 
-// Runs f() (which enqueues one kernel on st); with timing on, brackets it with events.
+// Runs f() (which enqueues one kernel on st); with GBD_TIMING_EVENTS it brackets the launch with
+// CUDA events, with GBD_TIMING_NVTX with an NVTX range named after the pass class.
+static const char* const kPassName[GBD_NPASS] = {"row_fwd", "row_inv", "row_rk", "film_conv",
+                                                 "y_fwd", "z_conv", "y_inv", "extrap_stage"};
 template <class F>
-static void timed(gbd_mesh* m, int pass, cudaStream_t st, F f) {
-  if (!m->timing) {
-    f();
-    return;
-  }
+static void timed_events(gbd_mesh* m, int pass, cudaStream_t st, F f) {
   if (m->used + 2 > m->events.size()) {
     size_t grow = m->events.size() < 256 ? 256 : m->events.size();
     for (size_t i = 0; i < grow; ++i) {
@@ -94,6 +94,19 @@ static void timed(gbd_mesh* m, int pass, cudaStream_t st, F f) {
   cudaEventRecord(m->events[m->used + 1], st);
   m->cls.push_back(pass);
   m->used += 2;
+}
+template <class F>
+static void timed(gbd_mesh* m, int pass, cudaStream_t st, F f) {
+  if (!m->timing) {
+    f();
+    return;
+  }
+  if (m->timing & GBD_TIMING_NVTX) nvtxRangePushA(kPassName[pass]);
+  if (m->timing & GBD_TIMING_EVENTS)
+    timed_events(m, pass, st, f);
+  else
+    f();
+  if (m->timing & GBD_TIMING_NVTX) nvtxRangePop();
 }
 
 namespace gbd {
@@ -448,7 +461,8 @@ gbd_status gbd_mesh_create(const gbd_mesh_desc* desc, gbd_mesh** out) {
 
 gbd_status gbd_mesh_set_timing(gbd_mesh* m, int enable) {
   if (!m) return fail(GBD_EINVAL, "mesh is NULL");
-  m->timing = enable != 0;
+  m->timing = enable & (GBD_TIMING_EVENTS | GBD_TIMING_NVTX);
+  if (enable != 0 && m->timing == 0) m->timing = GBD_TIMING_EVENTS;
   return GBD_OK;
 }
 
@@ -1433,8 +1447,8 @@ constexpr int kBatchBranches = 32;
 // gbd_llg_step's launch sequence for one mesh on one stream (no timing events).
 // gbd_llg_step_ex's launch sequence for one mesh on one stream, without timing events.
 void enqueue_llg(gbd_mesh* m, float* mm, int nsteps, double dt, unsigned flags, cudaStream_t st) {
-  const bool tmp = m->timing;
-  m->timing = false;
+  const int tmp = m->timing;
+  m->timing = 0;
   enqueue_llg_ex(m, mm, nsteps, dt, flags, st);
   m->timing = tmp;
 }

@@ -291,8 +291,13 @@ def gbd_batch_destroy(batch):
     _check(load().gbd_batch_destroy(batch))
 
 
+GBD_TIMING_EVENTS, GBD_TIMING_NVTX = 1, 2
+
+
 def gbd_mesh_set_timing(mesh, enable):
-    _check(load().gbd_mesh_set_timing(mesh, 1 if enable else 0))
+    """enable: False / True (CUDA events per launch) or GBD_TIMING_EVENTS | GBD_TIMING_NVTX bits."""
+    flags = enable if isinstance(enable, int) and not isinstance(enable, bool) else (GBD_TIMING_EVENTS if enable else 0)
+    _check(load().gbd_mesh_set_timing(mesh, int(flags)))
 
 
 def gbd_mesh_read_timing(mesh):

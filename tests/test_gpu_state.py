@@ -1,6 +1,7 @@
 """Checkpoint / resume of the integrator state kept in the mesh (gbd_mesh_get_state /
 gbd_mesh_set_state): an extrapolated RK4 run or an extrapolated RKF5(6) step sequence split by a
-save into a fresh mesh equals the unsplit run bit for bit; malformed images are refused."""
+save into a fresh mesh equals the unsplit run bit for bit; malformed images are refused. Also the
+per-launch tracing switch (CUDA events, NVTX ranges) leaves results unchanged."""
 import numpy as np
 import pytest
 
@@ -73,4 +74,24 @@ def test_malformed_state_refused(g):
     assert ei.value.status == g.GBD_EINVAL
     mesh.set_state(state)                            # the intact image still loads
     other.close()
+    mesh.close()
+
+
+def test_nvtx_tracing_leaves_results_and_event_timing_alone(g):
+    # GBD_TIMING_NVTX wraps each launch in an NVTX range; alone it records no events, and the
+    # field is the same as untraced
+    import torch
+    n, cell = (64, 32, 4), (3e-9, 3e-9, 3e-9)
+    M = to_dev(8e5 * W.random_unit(n, 44))
+    mesh = g.Mesh(n, cell, 8e5)
+    H0, H1 = torch.empty_like(M), torch.empty_like(M)
+    mesh.demag(M, H0)
+    g.gbd_mesh_set_timing(mesh.handle, g.GBD_TIMING_NVTX)
+    mesh.demag(M, H1)
+    assert sum(c for _, c in g.gbd_mesh_read_timing(mesh.handle).values()) == 0
+    g.gbd_mesh_set_timing(mesh.handle, g.GBD_TIMING_NVTX | g.GBD_TIMING_EVENTS)
+    mesh.demag(M, H1)
+    assert sum(c for _, c in g.gbd_mesh_read_timing(mesh.handle).values()) == 5
+    g.gbd_mesh_set_timing(mesh.handle, 0)
+    assert np.array_equal(to_host(H0), to_host(H1))
     mesh.close()
