@@ -106,3 +106,29 @@ def test_unit_norm_and_energy_decrease():
         E.append(_energy(m, Nf, cell, Ms, A))
     assert all(b <= a + 1e-12 * abs(a) for a, b in zip(E, E[1:]))
     assert E[-1] < E[0]
+
+
+def test_trajectory_error_hand_value():
+    """eps = sum_i |M(t_i) - M_ref(t_i)| / (n Ms) (Sec. II, Fig. 2 discussion) on a two-sample
+    trajectory worked out by hand: the differences (3, 4, 0) and (0, 5, 12) have Euclidean norms
+    5 and 13, so with Ms = 2 A/m eps = (5 + 13) / (2 * 2) = 4.5. Summing squared norms (97),
+    taking the norm of the whole difference (13.9 / 4), dropping Ms (9), dividing by n only, or
+    the largest sample instead of the mean (6.5) all give another number."""
+    ref = np.array([[1.0, 1.0, 1.0], [-2.0, 0.5, 3.0]])
+    traj = ref + np.array([[3.0, 4.0, 0.0], [0.0, 5.0, 12.0]])
+    assert L.trajectory_error(traj, ref, 2.0) == pytest.approx(4.5, rel=1e-15)
+    # symmetric in its two trajectories, zero for identical ones
+    assert L.trajectory_error(ref, traj, 2.0) == pytest.approx(4.5, rel=1e-15)
+    assert L.trajectory_error(ref, ref, 2.0) == 0.0
+
+
+def test_trajectory_error_unit_and_scaled_forms_agree():
+    """For trajectories of the normalised magnetization m = M / Ms the same measure is the mean
+    |m - m_ref|: scaling both trajectories by Ms and passing Ms changes nothing, and a constant
+    offset of length r along the whole trajectory gives r exactly."""
+    rng = np.random.default_rng(3)
+    ref = rng.standard_normal((40, 3))
+    off = np.array([0.0, 0.6, 0.8]) * 1e-3          # |off| = 1e-3
+    Ms = 8e5
+    assert L.trajectory_error(ref + off, ref, 1.0) == pytest.approx(1e-3, rel=1e-12)
+    assert L.trajectory_error(Ms * (ref + off), Ms * ref, Ms) == pytest.approx(1e-3, rel=1e-12)
