@@ -3,10 +3,13 @@
 * Thin film 1024 x 1024 x 1, 2 x 2 x 3 nm cells (vortex + noise state): gbd_demag element
   by element against the oracle's FP64 FFT convolution, and one gbd_llg_step (the call the
   benchmark times) against the oracle's RK4 step.
-* 3D mesh 512 x 512 x 64, 4 nm cubes: properties that hold at any size -- a uniformly
-  magnetized mesh has mean field -D M with D from Aharoni's prism formula; a single
-  magnetized cell j gives H_i = -Ms N(i - j) e_b, checked on sampled cells i against the
-  oracle's tensor evaluated one offset at a time.
+* 3D mesh 512 x 512 x 64, 4 nm cubes: the seeded random-unit-vector M of the benchmark,
+  element by element against the oracle's FP64 FFT convolution of the full mesh, for FP32
+  stages (e_inf <= 1e-5) and for split-BF16 (<= 1e-4) and split-FP16 (<= 1e-5) tensor-core
+  stages, each mesh autotuned as the benchmark does; and properties that hold at any size --
+  a uniformly magnetized mesh has mean field -D M with D from Aharoni's prism formula; a
+  single magnetized cell j gives H_i = -Ms N(i - j) e_b, checked on sampled cells i against
+  the oracle's tensor evaluated one offset at a time.
 """
 import numpy as np
 import pytest
@@ -105,3 +108,25 @@ def test_3d_single_cell_response_sampled(g, cube3d, j):
     ab = [[0, 3, 4], [3, 1, 5], [4, 5, 2]]
     want = np.stack([-spec.Ms * Nt[ab[a][b]] for a in range(3)])
     assert e_inf(Hs, want) <= TOL_FP32
+
+
+@pytest.fixture(scope="module")
+def random3d():
+    """The 512 x 512 x 64 random-M input and its FP64 oracle field (about a minute and ~30 GB
+    of host memory, once per module)."""
+    spec = W.large_3d()
+    M = (spec.Ms * W.random_unit(spec.n, spec.seed)).astype(np.float32)
+    Href = C.fft_conv(M.astype(np.float64), T.tensor_all_offsets(spec.n, spec.cell))
+    return spec, M, Href
+
+
+@pytest.mark.parametrize("prec,tol", [("GBD_FP32", TOL_FP32), ("GBD_SPLIT_BF16", 1e-4), ("GBD_SPLIT_FP16", 1e-5)])
+def test_3d_random_full_size(g, random3d, prec, tol):
+    spec, M, Href = random3d
+    mesh = g.Mesh(spec.n, spec.cell, spec.Ms, precision=getattr(g, prec))
+    mesh.autotune()
+    Hd = to_dev(np.zeros_like(M))
+    mesh.demag(to_dev(M), Hd)
+    err = e_inf(to_host(Hd), Href)
+    mesh.close()
+    assert err <= tol, (prec, err)
