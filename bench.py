@@ -145,7 +145,8 @@ def measured_peaks():
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in ("gbd_fft.cuh", "gbd_tc.cuh", "gbd_kernels.cuh", "gbd_launch.cuh", "gbd_row.cuh", "gbd_row.cu",
-              "gbd_conv.cuh", "gbd_conv.cu", "gbd_ypass.cu"):
+              "gbd_rowpipe.cuh", "gbd_conv.cuh", "gbd_conv.cu", "gbd_ypass.cuh", "gbd_ypass.cu", "gbd_mixed_row.cu",
+              "gbd_mixed_conv.cu"):
         with open(os.path.join(ROOT, "paper_2308_08447_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -185,6 +186,7 @@ def run_ours(args):
     nsteps = args.llg_steps
     m0 = W.vortex_noise(spec.n, spec.cell, spec.seed)
     mesh = gbdemag.Mesh(spec.n, spec.cell, spec.Ms, A_ex=spec.A_ex, alpha=spec.alpha)
+    mesh.autotune()   # tile variant per pass (set-up, before the timed region)
     m = torch.from_numpy(m0).cuda()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -250,7 +252,11 @@ def run_ours(args):
     dims = gbdemag.gbd_plan_dims(mesh.desc)
     bpl = film_bytes_per_launch(spec.n, dims[3], dims[4])
     top = max(passes, key=lambda k: passes[k][0])
-    avg_ms = passes[top][0] / passes[top][1]
+    # Events around every launch stretch each pass a little, so the average launch time of the
+    # top pass is taken from the uninstrumented timed region instead: its time per benchmark
+    # step times the pass's share of the instrumented step, over its launches per step.
+    share = {k: v[0] / sum(x[0] for x in passes.values()) for k, v in passes.items()}
+    avg_ms = ms_per_step * share[top] / passes[top][1]
     peak, peak_kind = measured_peaks()
     achieved = bpl[top] / (avg_ms * 1e-3) / 1e9
     launches_per_step = sum(c for _, c in passes.values())
@@ -258,8 +264,10 @@ def run_ours(args):
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": ncu_traffic(top), "algorithmic_bytes_per_launch": bpl[top],
                 "avg_launch_us": round(avg_ms * 1e3, 2),
-                "passes_us": {k: round(v[0] / v[1] * 1e3, 2) for k, v in passes.items()},
-                "share": {k: round(v[0] / sum(x[0] for x in passes.values()), 3) for k, v in passes.items()}}
+                "avg_launch_us_how": "uninstrumented step time x the pass's share of an event-instrumented step",
+                "passes_us_instrumented": {k: round(v[0] / v[1] * 1e3, 2) for k, v in passes.items()},
+                "tuning": list(gbdemag.gbd_mesh_get_tuning(mesh.handle)),
+                "share": {k: round(v, 3) for k, v in share.items()}}
 
     # the same run with the demag extrapolated at RK4 sub-steps (Sec. III; one demag evaluation
     # per step after four start-up steps), timed alike, and its end state against the exact run's
@@ -397,7 +405,7 @@ def run_batch(args):
     gbdemag.load()
     specs = W.batch_meshes(count=args.batch_count, seed=4, steps=args.llg_steps if args.llg_steps != 1000 else 100)
     t0 = time.perf_counter()
-    meshes = [gbdemag.Mesh(s.n, s.cell, s.Ms, A_ex=s.A_ex, alpha=s.alpha) for s in specs]
+    meshes = [gbdemag.Mesh(s.n, s.cell, s.Ms, A_ex=s.A_ex, alpha=s.alpha, pow2_pad=args.pow2_pad) for s in specs]
     tunings = [m.autotune() for m in meshes]
     setup_s = time.perf_counter() - t0
     init = [torch.from_numpy(W.random_unit(s.n, s.seed)).cuda() for s in specs]
@@ -446,6 +454,10 @@ def run_batch(args):
     clocks = sampler.stop()
     v_plain = evals * len(t_plain) / sum(t_plain) / 1e9
     v_batch = evals * len(t_batch) / sum(t_batch) / 1e9
+    # padded grid points of the meshes' plans against powers of two on every axis
+    vol = lambda d: d[0] * d[1] * d[2]
+    pad_vol = sum(vol(gbdemag.gbd_mesh_plan_dims(m.handle)) for m in meshes)
+    pad_vol2 = sum(vol(gbdemag.gbd_plan_dims(gbdemag.make_desc(s.n, s.cell, s.Ms, pow2_pad=True))) for s in specs)
     batch.close()
     for m in meshes:
         m.close()
@@ -460,6 +472,7 @@ def run_batch(args):
             "plain_path": {"value": round(v_plain, 3), "unit": UNIT,
                            "ms_per_step": round(1e3 * sum(t_plain) / len(t_plain), 3)},
             "speedup_vs_plain": round(v_batch / v_plain, 3), "results_bit_identical": bool(identical),
+            "padded_volume_vs_pow2": round(pad_vol / pad_vol2, 4),
             "tunings": {"%dx%dx%d" % s.n: list(t) for s, t in zip(specs, tunings)},
             "gpu_launches": sum(1 + 8 * n for n in steps) * args.steps, "clocks": clocks}
 
@@ -467,7 +480,11 @@ def run_batch(args):
 def run_serve(args):
     """Poisson arrivals (200 requests/s) of relaxation jobs (alpha = 0.5, 200-2000 steps, mesh
     sides log-uniform 64..1024, nz 1..16), admitted by a 150 GB budget, continuously batched;
-    latency percentiles and throughput against the plain path (each job alone, in order)."""
+    latency percentiles and throughput against the plain path (each job alone, in arrival order,
+    on the same trace). At 200 requests/s the offered load is many times what one GPU serves
+    (saturation: latency is queueing). With --rho r the same jobs are then served again at the
+    arrival rate r / s, s the plain path's mean service time measured in the saturated run (the
+    Poisson trace rescaled in time), labelled as the load factor r."""
     import numpy as np
     import torch
 
@@ -482,23 +499,41 @@ def run_serve(args):
     setup_s = time.perf_counter() - t0
     sampler = ClockSampler(0)
     sampler.start()
-    srv = serve.Server(ex, 150e9, chunk=args.chunk, max_active=args.max_active or None)
-    served = srv.run([serve.Job(j.id, j.spec, j.arrival) for j in jobs])
-    ex.close()
-    plain = serve.run_plain(ex, [serve.Job(j.id, j.spec, j.arrival) for j in jobs])
-    clocks = sampler.stop()
-    by_id = {j.id: j for j in plain}
-    identical = all(np.array_equal(j.result, by_id[j.id].result) for j in served)
-    s_served, s_plain = serve.summarize(served, args.extrap), serve.summarize(plain, args.extrap)
-    return {"metric": METRIC, "value": round(s_served["gcell_demag_per_s"], 3), "unit": UNIT, "n_gpus": 1,
-            "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "served: %d Poisson-arrival jobs at %.0f/s, continuous batching, %d-step chunks, "
-                                   "150 GB budget" % (len(jobs), args.rate, args.chunk),
-                       "max_active_cap": args.max_active or None, "setup_s": round(setup_s, 1),
-                       "demag_extrapolation": bool(args.extrap)},
-            "served": s_served, "plain_path": s_plain, "results_bit_identical": bool(identical),
-            "max_active": max(a for _, a, _ in srv.trace), "iterations": len(srv.trace), "clocks": clocks}
+
+    def one_trace(scale):
+        trace = [serve.Job(j.id, j.spec, j.arrival * scale) for j in jobs]
+        srv = serve.Server(ex, 150e9, chunk=args.chunk, max_active=args.max_active or None)
+        served = srv.run(trace)
+        ex.close()
+        plain = serve.run_plain(ex, [serve.Job(j.id, j.spec, j.arrival * scale) for j in jobs])
+        by_id = {j.id: j for j in plain}
+        identical = all(np.array_equal(j.result, by_id[j.id].result) for j in served)
+        for j in served + plain:
+            j.result = None
+        s_served, s_plain = serve.summarize(served, args.extrap), serve.summarize(plain, args.extrap)
+        busy = sum(j.finished - j.admitted for j in plain)   # the plain path runs one job at a time
+        return s_served, s_plain, identical, srv, busy
+
+    s_served, s_plain, identical, srv, busy = one_trace(1.0)
+    out = {"metric": METRIC, "value": round(s_served["gcell_demag_per_s"], 3), "unit": UNIT, "n_gpus": 1,
+           "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "served: %d Poisson-arrival jobs at %.0f/s, continuous batching, %d-step chunks, "
+                                  "150 GB budget" % (len(jobs), args.rate, args.chunk),
+                      "max_active_cap": args.max_active or None, "setup_s": round(setup_s, 1),
+                      "demag_extrapolation": bool(args.extrap)},
+           "served": s_served, "plain_path": s_plain, "results_bit_identical": bool(identical),
+           "plain_mean_service_s": round(busy / len(jobs), 4),
+           "max_active": max(a for _, a, _ in srv.trace), "iterations": len(srv.trace)}
+    if args.rho:
+        rate = args.rho * len(jobs) / busy
+        s2, p2, ident2, srv2, _ = one_trace(args.rate / rate)
+        out["load_%g" % args.rho] = {"rate_per_s": round(rate, 3),
+                                     "how": "rate = %g / (plain mean service time of the saturated run)" % args.rho,
+                                     "served": s2, "plain_path": p2, "results_bit_identical": bool(ident2),
+                                     "max_active": max(a for _, a, _ in srv2.trace), "iterations": len(srv2.trace)}
+    out["clocks"] = sampler.stop()
+    return out
 
 
 def run_3d(args):
@@ -515,14 +550,20 @@ def run_3d(args):
     torch.cuda.set_device(0)
     gbdemag.load()
     spec = W.large_3d()
+    if args.n3d:
+        spec.n = tuple(args.n3d)   # a smaller mesh of the same material (profiling)
     nsteps = 100
     m0 = W.random_unit(spec.n, spec.seed)
     res = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "data": "synthetic", "steps": args.steps, "warmup": args.warmup,
-           "config": {"workload": "3D 512x512x64, 4 nm cubes: 1 demag + %d RK4 steps, FP32 vs split-BF16 / split-FP16" % nsteps}}
+           "config": {"workload": "3D 512x512x64, 4 nm cubes: 1 demag + %d RK4 steps, FP32 vs split-BF16 / split-FP16" % nsteps,
+                      "l2": "inputs larger than L2 (M 201 MB, spectra 1.2 GB)"}}
     stream = torch.cuda.current_stream()
+    sampler = ClockSampler(0)
+    sampler.start()
     H = {}
     precs = (("fp32", gbdemag.GBD_FP32), ("split_bf16", gbdemag.GBD_SPLIT_BF16), ("split_fp16", gbdemag.GBD_SPLIT_FP16))
+    precs = tuple(p for p in precs if p[0] in args.precisions.split(","))
     for name, prec in precs:
         mesh = gbdemag.Mesh(spec.n, spec.cell, spec.Ms, A_ex=spec.A_ex, alpha=spec.alpha, precision=prec)
         mesh.autotune()
@@ -566,10 +607,12 @@ def run_3d(args):
                      "tuning": list(gbdemag.gbd_mesh_get_tuning(mesh.handle)), "passes": pass_info}
         res[name + "_m_after_100"] = m.cpu().numpy()
         mesh.close()
-    m32 = res.pop("fp32_m_after_100")
-    for name in ("split_bf16", "split_fp16"):
-        res[name]["m_after_100_max_abs_vs_fp32"] = float(np.abs(res.pop(name + "_m_after_100") - m32).max())
-    res["value"] = res["fp32"]["llg_gcell_demag_per_s"]
+    res["clocks"] = sampler.stop()
+    m32 = res.pop("fp32_m_after_100", None)
+    for name, _ in precs:
+        if name != "fp32" and m32 is not None:
+            res[name]["m_after_100_max_abs_vs_fp32"] = float(np.abs(res.pop(name + "_m_after_100") - m32).max())
+    res["value"] = res[precs[0][0]]["llg_gcell_demag_per_s"]
     res["dtype"] = "f32"
     if args.oracle_3d:
         from oracle import conv as C
@@ -580,19 +623,20 @@ def run_3d(args):
         for name, _ in precs:
             res[name]["demag_e_inf_vs_fp64_oracle"] = float(np.sqrt(((H[name] - Href) ** 2).sum(0)).max() / nrm)
         res["oracle_s"] = round(time.perf_counter() - t0, 1)
-    # 100 steps against the FP64 oracle on a 64 x 64 x 8 mesh of the same material
+    # RK4 steps against the FP64 oracle on a 64 x 64 x 8 mesh of the same material
     from oracle import llg as L
     from oracle import tensor as T
     small = (64, 64, 8)
+    csteps = args.check_steps
     ms0 = W.random_unit(small, spec.seed)
     Nf = T.tensor_all_offsets(small, spec.cell)
-    want = L.llg_run(ms0.astype(np.float64), nsteps, spec.dt, Nf, spec.cell, spec.Ms, spec.A_ex, spec.alpha)
+    want = L.llg_run(ms0.astype(np.float64), csteps, spec.dt, Nf, spec.cell, spec.Ms, spec.A_ex, spec.alpha)
     for name, prec in precs:
         mesh = gbdemag.Mesh(small, spec.cell, spec.Ms, A_ex=spec.A_ex, alpha=spec.alpha, precision=prec)
         m = torch.from_numpy(ms0).cuda()
-        mesh.llg_step(m, nsteps, spec.dt)
+        mesh.llg_step(m, csteps, spec.dt)
         got = m.cpu().numpy().astype(np.float64)
-        res[name]["llg_100_steps_64x64x8_max_abs_vs_fp64_oracle"] = float(np.abs(got - want).max())
+        res[name]["llg_%d_steps_64x64x8_max_abs_vs_fp64_oracle" % csteps] = float(np.abs(got - want).max())
         mesh.close()
     return res
 
@@ -677,6 +721,8 @@ def run_switching(args):
     from paper_2308_08447_gb300 import gbdemag
     from paper_2308_08447_gb300 import workloads as W
 
+    from oracle import llg as L   # the paper's error measure eps (pinned oracle function)
+
     torch.cuda.set_device(0)
     gbdemag.load()
     spec = W.switching()
@@ -710,18 +756,25 @@ def run_switching(args):
         torch.cuda.synchronize()
         return torch.stack(rec).double().cpu().numpy(), e0.elapsed_time(e1) / 1e3, per * n_rec
 
-    def run_rkf(tol, extrap=False):
+    def run_rkf(tol, extrap=False, host_loop=False):
+        # host_loop: per-launch timing on, which makes gbd_llg_run_rkf56 take its host-driven loop
+        # (a stream wait per attempt) instead of the device-controlled graph loop
         mm = mS.clone()
         rec, dt, acc, rej = [], 100e-15, 0, 0
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        if host_loop:
+            gbdemag.gbd_mesh_set_timing(mesh.handle, True)
+        t0 = time.perf_counter()
         for i in range(n_rec):
             dt, a_, r_ = mesh.run_rkf56(mm, interval, dt, tol, extrap=extrap, cont=extrap and i > 0)
             acc, rej = acc + a_, rej + r_
             rec.append(mm.mean(dim=(1, 2, 3)))
-        e1.record(stream)
+            if host_loop:
+                gbdemag.gbd_mesh_read_timing(mesh.handle)
         torch.cuda.synchronize()
-        return torch.stack(rec).double().cpu().numpy(), e0.elapsed_time(e1) / 1e3, acc, rej
+        secs = time.perf_counter() - t0
+        if host_loop:
+            gbdemag.gbd_mesh_set_timing(mesh.handle, False)
+        return torch.stack(rec).double().cpu().numpy(), secs, acc, rej
 
     ref, _, _ = run(25e-15, False)
     scaling = {}
@@ -730,19 +783,24 @@ def run_switching(args):
         row = {}
         for extrap in (False, True):
             traj, secs, steps = run(dt, extrap)
-            row["extrap" if extrap else "exact"] = float(np.linalg.norm(traj - ref, axis=1).sum() / n_rec)
+            row["extrap" if extrap else "exact"] = float(L.trajectory_error(traj, ref, 1.0))
             timing[(dt, extrap)] = (secs, steps)
         scaling["%g fs" % (dt * 1e15)] = row
     adaptive = {}
     for tol in (1e-4, 1e-5):
         for extrap in (False, True):
             traj, secs_a, acc, rej = run_rkf(tol, extrap)
-            adaptive["tol %g%s" % (tol, ", quintic demag extrapolation" if extrap else "")] = {
-                "eps": float(np.linalg.norm(traj - ref, axis=1).sum() / n_rec), "accepted": acc, "rejected": rej,
-                "mean_step_fs": round(t_end / acc * 1e15, 1), "s": round(secs_a, 3)}
+            row = {"eps": float(L.trajectory_error(traj, ref, 1.0)), "accepted": acc, "rejected": rej,
+                   "mean_step_fs": round(t_end / acc * 1e15, 1), "s": round(secs_a, 3)}
+            if not extrap:
+                _, secs_h, acc_h, rej_h = run_rkf(tol, False, host_loop=True)
+                row["s_host_driven_loop"] = round(secs_h, 3)
+                row["host_loop_steps"] = [acc_h, rej_h]
+            adaptive["tol %g%s" % (tol, ", quintic demag extrapolation" if extrap else "")] = row
     secs, steps = timing[(100e-15, False)]
     xsecs, xsteps = timing[(100e-15, True)]
     mesh.close()
+    fp64_study = switching_fp64_study()
     samples = {"%g ns" % (t * 1e9): [round(float(v), 5) for v in ref[int(round(t / interval)) - 1]]
                for t in (0.1e-9, 0.25e-9, 0.5e-9, 0.75e-9, 1e-9)}
     return {"metric": METRIC, "value": round(spec.cells * 4 * steps / secs / 1e9, 3), "unit": UNIT,
@@ -753,7 +811,68 @@ def run_switching(args):
                        "l2": "not flushed (1 ns of dynamics per run)"},
             "llg_steps_per_s": round(steps / secs, 1), "llg_steps_per_s_extrap": round(xsteps / xsecs, 1),
             "relax_s": round(relax_s, 2),
-            "eps_vs_25fs_exact": scaling, "adaptive_rkf56": adaptive, "mean_m_25fs_exact": samples}
+            "eps_vs_25fs_exact": scaling, "adaptive_rkf56": adaptive, "mean_m_25fs_exact": samples,
+            "eps_vs_fp64_oracle_96x48x2": fp64_study}
+
+
+def switching_fp64_study(dts=(400e-15, 200e-15, 100e-15, 50e-15, 25e-15)):
+    """The time-step study of Fig. 2 (Sec. II) against a double-precision reference: the switching
+    problem on the film reduced to 96 x 48 x 2 cells (same 5 nm cells and protocol), from the S
+    state the FP64 oracle relaxed, 1 ns under the switching field, <m> every 10 ps. The FP32 GPU
+    runs at each dt (exact and with the demag extrapolated at RK4 sub-steps) are compared with
+    the oracle's FP64 RK4 trajectory at 50 fs (both stored under tests/golden by
+    make_switching_reference.py) by the paper's mean error eps (oracle.llg.trajectory_error)."""
+    import numpy as np
+    import torch
+
+    from oracle import llg as L
+    from paper_2308_08447_gb300 import gbdemag
+    from paper_2308_08447_gb300 import workloads as W
+
+    gold = os.path.join(ROOT, "tests", "golden")
+    m_s = np.load(os.path.join(gold, "switching_96x48x2_S_state.npy"))
+    ref = np.loadtxt(os.path.join(gold, "switching_96x48x2_fp64_traj.txt"))
+    spec = W.switching(scale=5)
+    mesh = gbdemag.Mesh(spec.n, spec.cell, spec.Ms, A_ex=spec.A_ex, alpha=spec.alpha, Hext=spec.Hext)
+    interval, n_rec = 10e-12, len(ref)
+    out = {"reference": "FP64 oracle RK4 at 50 fs (its own eps against the 100 fs FP64 run: 1.1e-10)",
+           "mesh": "96x48x2 cells of 5 nm", "samples": n_rec}
+    for dt in dts:
+        row = {}
+        for extrap in (False, True):
+            m = torch.from_numpy(m_s).cuda()
+            per = int(round(interval / dt))
+            rec = []
+            for i in range(n_rec):
+                mesh.llg_step(m, per, dt, extrap=extrap, cont=extrap and i > 0)
+                rec.append(m.double().mean(dim=(1, 2, 3)))
+            traj = torch.stack(rec).cpu().numpy()
+            row["extrap" if extrap else "exact"] = float(L.trajectory_error(traj, ref, 1.0))
+        out["%g fs" % (dt * 1e15)] = row
+    mesh.close()
+    return out
+
+
+def run_extras(args):
+    """The rest of the metric beside the film headline, each with its own clock record: the 3D
+    mesh (FP32 and both split precisions, error against the FP64 oracle, per-pass rooflines),
+    the 64-mesh batch against the plain path, and a short served trace against the plain path."""
+    import copy
+    out = {}
+    a = copy.copy(args)
+    a.steps, a.warmup, a.oracle_3d, a.check_steps = 5, 2, True, 20
+    r = run_3d(a)
+    out["3d"] = {k: r[k] for k in ("config", "fp32", "split_bf16", "split_fp16", "oracle_s", "clocks") if k in r}
+    a = copy.copy(args)
+    a.steps, a.warmup, a.llg_steps = 2, 2, 100
+    r = run_batch(a)
+    out["batch"] = {k: r[k] for k in ("value", "unit", "ms_per_step", "config", "plain_path", "speedup_vs_plain",
+                                      "results_bit_identical", "padded_volume_vs_pow2", "clocks") if k in r}
+    a = copy.copy(args)
+    r = run_serve(a)
+    out["served"] = {k: r[k] for k in ("value", "unit", "config", "served", "plain_path", "results_bit_identical",
+                                       "max_active", "iterations", "clocks") if k in r}
+    return out
 
 
 def run_reference(args):
@@ -791,11 +910,18 @@ def main():
     ap.add_argument("--no-extrap", action="store_true", help="skip the demag-extrapolation run of the film")
     ap.add_argument("--workload", default="film", choices=["film", "batch", "serve", "3d", "cufft", "switching"])
     ap.add_argument("--oracle-3d", action="store_true", help="3d: FP64 oracle of the full mesh (minutes, ~30 GB)")
+    ap.add_argument("--check-steps", type=int, default=100, help="3d: RK4 steps of the 64x64x8 check against the oracle")
+    ap.add_argument("--n3d", type=int, nargs=3, default=None, help="3d: mesh size (default 512 512 64)")
+    ap.add_argument("--precisions", default="fp32,split_bf16,split_fp16", help="3d: which precisions to run")
+    ap.add_argument("--quick", action="store_true", help="film line only (no 3D / batch / served keys)")
     ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--pow2-pad", action="store_true", help="batch: power-of-two padded lengths only")
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--chunk", type=int, default=50)
     ap.add_argument("--max-active", type=int, default=8, help="served jobs per iteration (0: no cap)")
+    ap.add_argument("--rho", type=float, default=0.0,
+                    help="serve: also run the trace at this load factor of the plain path's service rate")
     ap.add_argument("--extrap", action="store_true",
                     help="serve: demag extrapolated at RK4 sub-steps on the served and the plain path")
     args = ap.parse_args()
@@ -813,6 +939,8 @@ def main():
         res = run_switching(args)
     else:
         res = run_ours(args)
+        if res is not None and res["n_gpus"] == 1 and not args.quick:
+            res.update(run_extras(args))
     if res is not None:
         print(json.dumps(res))
 

@@ -68,7 +68,7 @@ typedef struct {
   double gamma;          /* gyromagnetic ratio mu0*gamma_e, m/(A s); 0 selects 2.212761569e5 */
   double Hext[3];        /* uniform applied (Zeeman) field, A/m */
   int precision;         /* gbd_precision */
-  unsigned flags;        /* GBD_FLAG_PBC_* bits (0: open boundaries everywhere) */
+  unsigned flags;        /* GBD_FLAG_PBC_* and GBD_FLAG_POW2_PAD bits (0: open boundaries, shortest padding) */
   int pbc_images;        /* periodic images per side along each periodic axis (>= 1 with one) */
 } gbd_mesh_desc;
 
@@ -83,11 +83,18 @@ typedef struct {
 #define GBD_FLAG_PBC_X 1u
 #define GBD_FLAG_PBC_Y 2u
 #define GBD_FLAG_PBC_Z 4u
+/* Padded lengths (Sec. II pads each open axis to 2n; any length >= 2n - 1 gives the same
+ * cropped result). By default an FP32 mesh pads x and y to the smallest length >= 2n - 1 among
+ * the powers of two and the lengths 3 * 2^k, 5 * 2^k that have kernels (x: 2 Lx with
+ * Lx in {96, 160, 192, 320, 384, 640, 768, 1280, 1536, 2560, 3072}; y: those values), which
+ * is up to 37.5 % shorter per axis than the next power of two; z, periodic axes and the split
+ * precisions use powers of two. GBD_FLAG_POW2_PAD forces powers of two on every axis. */
+#define GBD_FLAG_POW2_PAD 8u
 
 typedef struct gbd_mesh gbd_mesh; /* opaque: plan, kernel spectrum, scratch, RK4 state */
 
-/* Validates desc, plans the padded lengths (powers of two >= 2n - 1; 1 where n = 1; n along a
- * periodic axis) and
+/* Validates desc, plans the padded lengths (>= 2n - 1, see GBD_FLAG_POW2_PAD; 1 where n = 1;
+ * n along a periodic axis) and
  * allocates the mesh's device buffers on the current device: x spectrum, 3D y spectrum,
  * kernel spectrum, RK4 scratch, twiddle table. *out receives the mesh (NULL on failure).
  * Errors: GBD_EINVAL, GBD_EUNSUPPORTED, GBD_ENOMEM, GBD_ECUDA. On any error every buffer
@@ -191,8 +198,9 @@ gbd_status gbd_mesh_set_params(gbd_mesh* mesh, const double Hext[3], double alph
  * [3][nz][ny][nx] float32 for each history the mesh has allocated). gbd_mesh_get_state waits
  * for stream, then copies the state into host (bytes >= that size, else GBD_EINVAL).
  * gbd_mesh_set_state waits for stream and replaces the mesh's state by an image from a mesh
- * with the same number of cells (GBD_EINVAL for a malformed or foreign image, which changes
- * nothing); a following call with GBD_STEP_CONTINUE resumes exactly where the saved mesh
+ * of the same shape (nx, ny, nz) and periodic axes (GBD_EINVAL for a malformed or foreign
+ * image, which changes nothing; a CUDA error while copying returns GBD_ECUDA and discards the
+ * mesh's histories, so the next extrapolated call starts them afresh); a following call with GBD_STEP_CONTINUE resumes exactly where the saved mesh
  * stood, so a run split by get/set (even across processes) equals the unsplit run bit for
  * bit. Both block the host. */
 gbd_status gbd_mesh_state_bytes(const gbd_mesh* mesh, size_t* out);
@@ -216,8 +224,9 @@ gbd_status gbd_mesh_set_state(gbd_mesh* mesh, const void* host, size_t bytes, vo
  *     exceed GBD_NOALLOC_MAX_BYTES; a larger mesh is refused with GBD_EBUDGET before any
  *     work is enqueued. Every GPU that loads the library holds this array until exit.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
- *     with that device current) and caches it; make that first call before any stream
- *     capture.
+ *     with that device current) and caches it; with lazy module loading that lookup may also
+ *     load the library's device code, and with it the array, onto the device. Make that first
+ *     call before any stream capture.
  *   - All calls on a device share the one array, which keeps the last call's contents. Each
  *     call writes every scratch element before reading it, so nothing needs clearing; but
  *     calls whose work overlaps on the GPU (different streams, other meshes) race on it and
@@ -226,23 +235,41 @@ gbd_status gbd_mesh_set_state(gbd_mesh* mesh, const void* host, size_t bytes, vo
 #define GBD_NOALLOC_MAX_BYTES (64u << 20)
 gbd_status gbd_demag_noalloc(gbd_mesh* mesh, const float* M, float* H, void* stream);
 
-/* Frees the mesh's device buffers (after synchronizing the device). NULL is accepted. */
+/* Frees the mesh's device buffers without waiting: the frees are stream-ordered (the device's
+ * memory pool, cudaFreeAsync) after the last work each stream was given for this mesh by the
+ * calls above and by batch runs, so other work on the device is not stalled and the host
+ * returns at once. Work that the caller captured into its own CUDA graphs must have finished
+ * before this call. The mesh's buffers come from the same pool (cudaMallocAsync). NULL is
+ * accepted. */
 gbd_status gbd_mesh_destroy(gbd_mesh* mesh);
 
 /* Message of the calling thread's last failure ("" if none). Valid until its next call. */
 const char* gbd_last_error(void);
 
 /* ---- tile-shape autotuning ---------------------------------------------------------------
- * Every kernel family has two tile shapes (lines of the transform per thread block). They
- * give identical results -- each line's FFT and each cell's update do not depend on how lines
- * are grouped -- and differ only in speed, which depends on the mesh size. gbd_mesh_autotune
- * times both shapes of each pass this mesh uses (on its own buffers, which it zeroes; the
- * stream is synchronized) and keeps the faster; results are cached per (nx, ny, nz, device)
- * in the process and, when the environment variable GBD_AUTOTUNE_CACHE names a file, in that
- * text file. Requires gbd_set_kernel. Variants (row, film, y, z) are each 0 or 1. */
+ * Every kernel family has two tile shapes (lines of the transform per thread block); the x-row
+ * pass has a third variant, 2 (FP32 meshes): a persistent kernel, one block per SM, that copies
+ * the next row group's spectrum tile and field rows into shared memory (cp.async) while it
+ * transforms the current group, used where it applies (x transform length Px/2 in [64, 2048],
+ * open x axis, nx a multiple of 4, ny a multiple of the group's rows, the staged fields
+ * 16-byte aligned; otherwise variant 1 runs). A new mesh starts with variant 1 everywhere. All variants give identical
+ * results -- each line's FFT and each cell's update do not depend on how lines are grouped --
+ * and differ only in speed, which depends on the mesh size. gbd_mesh_autotune times the
+ * variants of each pass this mesh uses (on its own buffers, which it zeroes; the stream is
+ * synchronized) and keeps the fastest; results are cached per (nx, ny, nz, device) in the
+ * process and, when the environment variable GBD_AUTOTUNE_CACHE names a file, in that text
+ * file. Requires gbd_set_kernel. Variants (row, film, y, z): row 0, 1 or 2, the others 0 or 1.
+ * The autotuner also chooses the padded lengths: a mesh planned with a 3 * 2^k or 5 * 2^k
+ * length (see GBD_FLAG_POW2_PAD) is timed against the same mesh on power-of-two lengths (a
+ * scratch twin with its own tuned tiles), and moves onto the power-of-two plan when that is
+ * more than 2 % faster: new spectrum buffers, the kernel spectrum recomputed for the new
+ * lengths (the cropped result is the same, Sec. II), GBD_FLAG_POW2_PAD then set in its
+ * description. gbd_mesh_plan_dims gives the lengths a mesh uses. */
 gbd_status gbd_mesh_autotune(gbd_mesh* mesh, void* stream);
 gbd_status gbd_mesh_get_tuning(const gbd_mesh* mesh, int out[4]);
 gbd_status gbd_mesh_set_tuning(gbd_mesh* mesh, const int in[4]);
+/* The plan a mesh uses now: out = {Px, Py, Pz, Hx, Ky, Kz}, as gbd_plan_dims. */
+gbd_status gbd_mesh_plan_dims(const gbd_mesh* mesh, int out[6]);
 
 /* ---- batched meshes ------------------------------------------------------------------------
  * A batch advances many independent meshes (uneven sizes allowed) with one CUDA-graph launch
@@ -272,7 +299,8 @@ gbd_status gbd_batch_run(gbd_batch* batch, float* const* m, const int* nsteps, c
 gbd_status gbd_batch_run_ex(gbd_batch* batch, float* const* m, const int* nsteps, const double* dt,
                             const unsigned* flags, void* stream);
 
-/* Synchronizes the device and frees the batch (not the meshes). NULL is accepted. */
+/* Waits for the batch's last graph launch (not the rest of the device) and frees the batch
+ * (not the meshes). NULL is accepted. */
 gbd_status gbd_batch_destroy(gbd_batch* batch);
 
 /* ---- per-pass timing ------------------------------------------------------------------- */

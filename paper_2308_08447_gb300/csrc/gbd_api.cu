@@ -51,12 +51,17 @@ struct gbd_mesh {
   int hist_count = 0, hist_head = 0;
   double hist_dt = 0.0;
   unsigned version = 0;     // bumped when launch arguments change (params, tuning): batch graphs re-capture
-  // RKF5(6) stepping (allocated on first use): 8 stage slopes [3][N] each, the step's result,
-  // the error word and its pinned host copy
+  // RKF5(6) stepping (allocated on first use): 8 stage slopes [3][N] each, the step's result
+  // and the error word
   float* rk_k = nullptr;
   float* rk_m = nullptr;
   unsigned* rk_err = nullptr;
-  unsigned* rk_err_host = nullptr;
+  // device-controlled run (gbd_llg_run_rkf56 without extrapolation): the control block and the
+  // instantiated loop graph, built for the array rkf_key_m at parameter version rkf_key_version
+  gbd::RkfCtl* rk_ctl = nullptr;
+  cudaGraphExec_t rkf_exec = nullptr;
+  const float* rkf_key_m = nullptr;
+  unsigned rkf_key_version = 0;
   // demag history of RKF5(6) with extrapolation: 6 slots of [3][N]; rk_ring holds the slots of
   // the accepted step starts, newest first (rk_count valid), rk_ring_t their times relative to
   // the current time; rk_pend receives the field of the step being tried
@@ -70,6 +75,10 @@ struct gbd_mesh {
   std::vector<cudaEvent_t> events;
   std::vector<int> cls;
   size_t used = 0;
+  // the last work each stream was given for this mesh (recorded after every call that enqueues
+  // work outside a stream capture, and after batch graph launches); gbd_mesh_destroy orders the
+  // frees after these
+  std::vector<std::pair<cudaStream_t, cudaEvent_t>> done;
 };
 
 // Runs f() (which enqueues one kernel on st); with GBD_TIMING_EVENTS it brackets the launch with
@@ -117,7 +126,14 @@ static int pow2_at_least(long long v) {
   return p;
 }
 
-bool make_plan(int nx, int ny, int nz, int per, Plan& p, const char** why) {
+// The smallest mixed length L (kMixedLens) with L >= v, or 0.
+static int mixed_at_least(long long v) {
+  for (int L : kMixedLens)
+    if (L >= v) return L;
+  return 0;
+}
+
+bool make_plan(int nx, int ny, int nz, int per, bool mixed, Plan& p, const char** why) {
   if (nx < 1 || ny < 1 || nz < 1) {
     *why = "mesh sizes must be >= 1";
     return false;
@@ -144,6 +160,14 @@ bool make_plan(int nx, int ny, int nz, int per, Plan& p, const char** why) {
   // periodic: the period itself (circular convolution); otherwise zero padded
   p.Px = (per & 1) ? nx : (nx == 1 ? 2 : pow2_at_least(2LL * nx - 1));
   p.Py = (per & 2) ? ny : (ny == 1 ? 1 : pow2_at_least(2LL * ny - 1));
+  if (mixed && !(per & 1) && nx > 1) {
+    const int lx = mixed_at_least(nx);   // 2 Lx >= 2 nx - 1
+    if (lx && 2 * lx < p.Px) p.Px = 2 * lx;
+  }
+  if (mixed && !(per & 2) && ny > 1) {
+    const int ly = mixed_at_least(2LL * ny - 1);
+    if (ly && ly < p.Py) p.Py = ly;
+  }
   p.Pz = (per & 4) ? nz : (nz == 1 ? 1 : pow2_at_least(2LL * nz - 1));
   p.ox = (per & 1) ? nx / 2 + 1 : nx;
   p.oy = (per & 2) ? ny / 2 + 1 : ny;
@@ -166,7 +190,7 @@ bool make_plan(int nx, int ny, int nz, int per, Plan& p, const char** why) {
   p.bytes_T = (!p.film && ny > 1) ? (size_t)3 * nz * p.Hx * p.Py * sizeof(float2) : 0;
   p.bytes_K = p.film ? (size_t)p.Hx * p.Ky * sizeof(float4) : (size_t)p.Hx * p.Ky * p.Kz * 6 * sizeof(float);
   p.bytes_state = (size_t)3 * 3 * p.N * sizeof(float);
-  p.bytes_tw = (size_t)(2 * GBD_TW_LEN + GBD_TC_FRAG_F2) * sizeof(float2);
+  p.bytes_tw = (size_t)GBD_TW_TOTAL * sizeof(float2);
   return true;
 }
 
@@ -188,12 +212,14 @@ static gbd_status check_desc(const gbd_mesh_desc* d, gbd::Plan& p) {
     if (!std::isfinite(d->Hext[i])) return fail(GBD_EINVAL, "Hext must be finite");
   if (d->precision != GBD_FP32 && d->precision != GBD_SPLIT_BF16 && d->precision != GBD_SPLIT_FP16)
     return fail(GBD_EINVAL, "precision must be GBD_FP32, GBD_SPLIT_BF16 or GBD_SPLIT_FP16");
-  if (d->flags & ~(unsigned)(GBD_FLAG_PBC_X | GBD_FLAG_PBC_Y | GBD_FLAG_PBC_Z))
+  if (d->flags & ~(unsigned)(GBD_FLAG_PBC_X | GBD_FLAG_PBC_Y | GBD_FLAG_PBC_Z | GBD_FLAG_POW2_PAD))
     return fail(GBD_EINVAL, "unknown flags");
   const int per = (int)(d->flags & 7u);
   if (per && (d->pbc_images < 1 || d->pbc_images > kMaxImages))
     return fail(GBD_EINVAL, "pbc_images must be in [1, " + std::to_string(kMaxImages) + "] with a periodic axis");
-  if (!gbd::make_plan(d->nx, d->ny, d->nz, per, p, &why)) return fail(GBD_EUNSUPPORTED, why);
+  // lengths 3 * 2^k and 5 * 2^k have FP32 kernels only
+  const bool mixed = d->precision == GBD_FP32 && !(d->flags & GBD_FLAG_POW2_PAD);
+  if (!gbd::make_plan(d->nx, d->ny, d->nz, per, mixed, p, &why)) return fail(GBD_EUNSUPPORTED, why);
   p.images = per ? d->pbc_images : 0;
   p.prec = (d->precision == GBD_SPLIT_BF16) ? 1 : (d->precision == GBD_SPLIT_FP16) ? 2 : 0;
   return GBD_OK;
@@ -211,31 +237,84 @@ static gbd_status check_device(const gbd_mesh* m) {
   return GBD_OK;
 }
 
+// Device memory of meshes comes from the device's stream-ordered pool (cudaMallocAsync /
+// cudaFreeAsync) on a library stream per device, so that creating or destroying a mesh never
+// waits for the whole device (cudaMalloc / cudaFree do): an allocation is made on the library
+// stream and that stream is synchronized before the memory is handed out; a free is ordered
+// after the mesh's own recorded work and returns at once.
+static cudaStream_t lib_stream(int dev) {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {nullptr};
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    streams[dev] = nullptr;
+  }
+  return streams[dev];
+}
+
+// Allocates `bytes` for a mesh on device dev and waits until the memory is usable by any stream.
+static cudaError_t mesh_alloc(int dev, void** ptr, size_t bytes) {
+  cudaStream_t ls = lib_stream(dev);
+  cudaError_t e = cudaMallocAsync(ptr, bytes, ls);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ls);
+  return e;
+}
+
 static void free_mesh_buffers(gbd_mesh* m) {
-  cudaFree(m->S);
-  cudaFree(m->T);
-  cudaFree(m->K);
-  cudaFree(m->acc);
-  cudaFree(m->bufA);
-  cudaFree(m->bufB);
-  cudaFree(m->tw);
-  cudaFree(m->hist);
+  cudaStream_t ls = lib_stream(m->device);
+  for (auto& d : m->done) {
+    cudaStreamWaitEvent(ls, d.second, 0);
+    cudaEventDestroy(d.second);
+  }
+  m->done.clear();
+  if (m->rkf_exec) cudaGraphExecDestroy(m->rkf_exec);   // never running here: its call waited for it
+  m->rkf_exec = nullptr;
+  void* bufs[] = {m->S, m->T, m->K, m->acc, m->bufA, m->bufB, m->tw, m->hist, m->rk_k, m->rk_m, m->rk_err, m->rk_hist,
+                  m->rk_ctl};
+  for (void* b : bufs)
+    if (b) cudaFreeAsync(b, ls);
   m->hist = nullptr;
-  cudaFree(m->rk_k);
-  cudaFree(m->rk_m);
-  cudaFree(m->rk_err);
-  cudaFreeHost(m->rk_err_host);
-  cudaFree(m->rk_hist);
   m->rk_hist = nullptr;
   m->rk_k = m->rk_m = nullptr;
-  m->rk_err = m->rk_err_host = nullptr;
+  m->rk_err = nullptr;
+  m->rk_ctl = nullptr;
   m->S = m->T = nullptr;
   m->K = nullptr;
   m->acc = m->bufA = m->bufB = nullptr;
   m->tw = nullptr;
 }
 
+// Records the end of the work just enqueued for m on st (not inside a stream capture: captured
+// work is run by the caller's graph, which the caller finishes before destroying the mesh).
+static void mark_done(gbd_mesh* m, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;
+  }
+  for (auto& d : m->done)
+    if (d.first == st) {
+      cudaEventRecord(d.second, st);
+      return;
+    }
+  cudaEvent_t ev;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  cudaEventRecord(ev, st);
+  m->done.emplace_back(st, ev);
+}
+
 // ---- launch sequences ------------------------------------------------------------------------
+
+// Tile variant of an x-row launch: the transform-only launches (forward, or inverse to H_d) and
+// the launches with an epilogue are tuned separately.
+static int row_var(const gbd_mesh* m, int mode) {
+  return (mode == gbd::ROW_FWD || mode == gbd::ROW_H) ? m->p.var_row_io : m->p.var_row;
+}
 
 static gbd::RowArgs row_args(const gbd_mesh* m) {
   const gbd::Plan& p = m->p;
@@ -406,28 +485,35 @@ gbd_status gbd_mesh_create(const gbd_mesh_desc* desc, gbd_mesh** out) {
   int nalloc = 0;
   for (auto& al : allocs) {
     if (al.bytes == 0) continue;
-    e = (++nalloc == fail_at) ? cudaErrorMemoryAllocation : cudaMalloc(al.ptr, al.bytes);
+    e = (++nalloc == fail_at) ? cudaErrorMemoryAllocation : mesh_alloc(m->device, al.ptr, al.bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
       free_mesh_buffers(m);
+      cudaStreamSynchronize(lib_stream(m->device));   // the pool gives the memory back at this point
       delete m;
       return fail(e == cudaErrorMemoryAllocation ? GBD_ENOMEM : GBD_ECUDA,
-                  std::string("cudaMalloc: ") + cudaGetErrorString(e));
+                  std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
     }
   }
-  // twiddle levels: exp(-2 pi i m / N) at index N + m for N = 1, 2, 4, ..., GBD_TW_LEN and
-  // m < N, FP64 on the host, rounded to FP32 (index 0 is unused)
-  // (the split DFT-16 fragment tables after them are written on the device below)
-  std::vector<float2> tw(2 * GBD_TW_LEN, make_float2(1.f, 0.f));
-  for (int N = 1; N <= GBD_TW_LEN; N *= 2)
+  // twiddle levels: exp(-2 pi i m / N) at index tw_base(N) + m for m < N and N = 1, 2, 4, ...,
+  // GBD_TW_LEN, N = 3, 6, ..., GBD_TW3_MAX and N = 5, 10, ..., GBD_TW5_MAX, FP64 on the host,
+  // rounded to FP32 (the split DFT-16 fragment tables between them are written on the device
+  // below)
+  std::vector<float2> tw(GBD_TW_TOTAL, make_float2(1.f, 0.f));
+  auto level = [&](int N) {
     for (int k = 0; k < N; ++k) {
       const double ang = -2.0 * 3.14159265358979323846264338327950288 * (double)k / N;
-      tw[N + k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+      tw[gbd::tw_base(N) + k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
     }
-  e = cudaMemcpy(m->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  };
+  for (int N = 1; N <= GBD_TW_LEN; N *= 2) level(N);
+  for (int N = 3; N <= GBD_TW3_MAX; N *= 2) level(N);
+  for (int N = 5; N <= GBD_TW5_MAX; N *= 2) level(N);
+  cudaStream_t ls = lib_stream(m->device);
+  e = cudaMemcpyAsync(m->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, ls);
   if (e == cudaSuccess) {
-    gbd::launch_dft16_frags(m->tw + 2 * GBD_TW_LEN, nullptr);
-    e = cudaStreamSynchronize(nullptr);
+    gbd::launch_dft16_frags(m->tw + 2 * GBD_TW_LEN, ls);
+    e = cudaStreamSynchronize(ls);
     if (e == cudaSuccess) e = cudaGetLastError();
   }
   if (e != cudaSuccess) {
@@ -499,9 +585,12 @@ gbd_status gbd_mesh_set_params(gbd_mesh* m, const double Hext[3], double alpha) 
 
 gbd_status gbd_mesh_destroy(gbd_mesh* m) {
   if (!m) return GBD_OK;
-  cudaDeviceSynchronize();
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != m->device) cudaSetDevice(m->device);
   for (cudaEvent_t e : m->events) cudaEventDestroy(e);
-  free_mesh_buffers(m);
+  free_mesh_buffers(m);   // ordered after the mesh's recorded work; the host does not wait
+  if (prev != m->device && prev >= 0) cudaSetDevice(prev);
   delete m;
   return GBD_OK;
 }
@@ -514,7 +603,11 @@ struct GeoKey {
   int nx, ny, nz;
   double dx, dy, dz;
   int per, images;   // periodic axes and images per side
+  int Px, Py, Pz;    // padded lengths (the spectrum is sampled on them)
   bool operator<(const GeoKey& o) const {
+    if (Px != o.Px) return Px < o.Px;
+    if (Py != o.Py) return Py < o.Py;
+    if (Pz != o.Pz) return Pz < o.Pz;
     if (nx != o.nx) return nx < o.nx;
     if (ny != o.ny) return ny < o.ny;
     if (nz != o.nz) return nz < o.nz;
@@ -606,7 +699,7 @@ gbd_status gbd_set_kernel(gbd_mesh* m, void* stream) {
   gbd_status s = check_device(m);
   if (s != GBD_OK) return s;
   const gbd::Plan& p = m->p;
-  const GeoKey key{p.nx, p.ny, p.nz, m->d.dx, m->d.dy, m->d.dz, p.per, p.images};
+  const GeoKey key{p.nx, p.ny, p.nz, m->d.dx, m->d.dy, m->d.dz, p.per, p.images, p.Px, p.Py, p.Pz};
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (auto hit = spec_cache_get(key)) {
     cudaError_t e = cudaMemcpyAsync(m->K, hit->data(), p.bytes_K, cudaMemcpyHostToDevice, st);
@@ -658,13 +751,14 @@ gbd_status gbd_demag(gbd_mesh* m, const float* M, float* H, void* stream) {
   a.in = M;
   a.mode = gbd::ROW_FWD;
   a.fwd_after = 1;
-  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
+  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, row_var(m, a.mode), m->p.prec, a, m->tw, st); });
   enqueue_conv(m, st);
   a.hscale = 1.f;
   a.out = H;
   a.mode = gbd::ROW_H;
   a.fwd_after = 0;
-  timed(m, GBD_PASS_ROW_INV, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
+  timed(m, GBD_PASS_ROW_INV, st, [&] { gbd::launch_row(m->p.Lx, row_var(m, a.mode), m->p.prec, a, m->tw, st); });
+  mark_done(m, st);
   return after_launch("gbd_demag");
 }
 
@@ -677,13 +771,14 @@ static gbd_status field_like(gbd_mesh* m, const float* mm, float* out, int mode,
   a.in = mm;
   a.mode = gbd::ROW_FWD;
   a.fwd_after = 1;
-  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
+  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, row_var(m, a.mode), m->p.prec, a, m->tw, st); });
   enqueue_conv(m, st);
   a.ms = mm;
   a.out = out;
   a.mode = mode;
   a.fwd_after = 0;
-  timed(m, GBD_PASS_ROW_INV, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
+  timed(m, GBD_PASS_ROW_INV, st, [&] { gbd::launch_row(m->p.Lx, row_var(m, a.mode), m->p.prec, a, m->tw, st); });
+  mark_done(m, st);
   return after_launch(name);
 }
 
@@ -712,7 +807,7 @@ static void extrap_weights(double c, float w[5]) {
 // Allocates the mesh's extrapolation history on first use (never inside a stream capture).
 static gbd_status ensure_history(gbd_mesh* m) {
   if (m->hist) return GBD_OK;
-  cudaError_t e = cudaMalloc(&m->hist, (size_t)5 * 3 * m->p.N * sizeof(float));
+  cudaError_t e = mesh_alloc(m->device, (void**)&m->hist, (size_t)5 * 3 * m->p.N * sizeof(float));
   if (e != cudaSuccess) {
     cudaGetLastError();
     m->hist = nullptr;
@@ -741,7 +836,7 @@ static void enqueue_llg_ex(gbd_mesh* m, float* mm, int nsteps, double dt, unsign
   a.in = mm;
   a.mode = gbd::ROW_FWD;
   a.fwd_after = 1;
-  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
+  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, row_var(m, a.mode), m->p.prec, a, m->tw, st); });
   a.m0 = mm;
   a.m0_out = mm;
   a.acc = m->acc;
@@ -780,7 +875,7 @@ static void enqueue_llg_ex(gbd_mesh* m, float* mm, int nsteps, double dt, unsign
       if (a.extrap && !a.fwd_after)
         timed(m, GBD_PASS_EXTRAP, st, [&] { gbd::launch_extrap_stage(a, st); });
       else
-        timed(m, GBD_PASS_ROW_RK, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
+        timed(m, GBD_PASS_ROW_RK, st, [&] { gbd::launch_row(m->p.Lx, row_var(m, a.mode), m->p.prec, a, m->tw, st); });
     }
   }
 }
@@ -798,6 +893,7 @@ gbd_status gbd_llg_step_ex(gbd_mesh* m, float* mm, int nsteps, double dt, unsign
     if (s != GBD_OK) return s;
   }
   enqueue_llg_ex(m, mm, nsteps, dt, flags, static_cast<cudaStream_t>(stream));
+  mark_done(m, static_cast<cudaStream_t>(stream));
   return after_launch("gbd_llg_step");
 }
 
@@ -836,7 +932,7 @@ static void rkf_accept(gbd_mesh* m, double h, bool extrap) {
 
 static gbd_status ensure_rkf_history(gbd_mesh* m) {
   if (m->rk_hist) return GBD_OK;
-  cudaError_t e = cudaMalloc(&m->rk_hist, (size_t)6 * 3 * m->p.N * sizeof(float));
+  cudaError_t e = mesh_alloc(m->device, (void**)&m->rk_hist, (size_t)6 * 3 * m->p.N * sizeof(float));
   if (e != cudaSuccess) {
     cudaGetLastError();
     m->rk_hist = nullptr;
@@ -849,26 +945,29 @@ static gbd_status ensure_rkf_history(gbd_mesh* m) {
 static gbd_status ensure_rkf(gbd_mesh* m) {
   if (m->rk_k) return GBD_OK;
   const size_t n3 = (size_t)3 * m->p.N;
-  cudaError_t e = cudaMalloc(&m->rk_k, 8 * n3 * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&m->rk_m, n3 * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&m->rk_err, sizeof(unsigned));
-  if (e == cudaSuccess) e = cudaMallocHost(&m->rk_err_host, sizeof(unsigned));
+  cudaError_t e = mesh_alloc(m->device, (void**)&m->rk_k, 8 * n3 * sizeof(float));
+  if (e == cudaSuccess) e = mesh_alloc(m->device, (void**)&m->rk_m, n3 * sizeof(float));
+  if (e == cudaSuccess) e = mesh_alloc(m->device, (void**)&m->rk_err, sizeof(unsigned));
   if (e != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(m->rk_k);
-    cudaFree(m->rk_m);
-    cudaFree(m->rk_err);
+    cudaStream_t ls = lib_stream(m->device);
+    if (m->rk_k) cudaFreeAsync(m->rk_k, ls);
+    if (m->rk_m) cudaFreeAsync(m->rk_m, ls);
+    if (m->rk_err) cudaFreeAsync(m->rk_err, ls);
+    cudaStreamSynchronize(ls);
     m->rk_k = m->rk_m = nullptr;
     m->rk_err = nullptr;
-    m->rk_err_host = nullptr;
     return fail(e == cudaErrorMemoryAllocation ? GBD_ENOMEM : GBD_ECUDA, "RKF5(6) buffer allocation");
   }
   return GBD_OK;
 }
 
-// One RKF5(6) step of size h from mm: the normalized fifth-order result into m->rk_m and the
-// error estimate h max_cells |sum_i (b6_i - b5_i) k_i| into *err (waits for the stream).
-static gbd_status rkf_step(gbd_mesh* m, const float* mm, double h, cudaStream_t st, double* err, bool extrap) {
+// Enqueues one RKF5(6) attempt of size h from mm on st: the normalized fifth-order result into
+// m->rk_m and the largest error norm |sum_i (b6_i - b5_i) k_i| (float bits) into *err_word, which
+// must be zero beforehand. With hdev the step size is read on the device (*hdev, FP32; h is not
+// used) and there is no extrapolation.
+static void rkf_enqueue_attempt(gbd_mesh* m, const float* mm, double h, const float* hdev, unsigned* err_word,
+                                cudaStream_t st, bool extrap) {
   const size_t n3 = (size_t)3 * m->p.N;
   float* k[8];
   for (int i = 0; i < 8; ++i) k[i] = m->rk_k + i * n3;
@@ -884,11 +983,12 @@ static gbd_status rkf_step(gbd_mesh* m, const float* mm, double h, cudaStream_t 
       hsrc[q + 1] = m->rk_hist + (size_t)m->rk_ring[q] * n3;
     }
   }
+  const double hk = hdev ? 1.0 : h;   // factor folded into the weights on the host
   gbd::RowArgs a = row_args(m);
   a.in = mm;
   a.mode = gbd::ROW_FWD;
   a.fwd_after = 1;
-  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
+  timed(m, GBD_PASS_ROW_FWD, st, [&] { gbd::launch_row(m->p.Lx, row_var(m, a.mode), m->p.prec, a, m->tw, st); });
   float* stage_in[2] = {m->bufA, m->bufB};
   const float* ms = mm;
   for (int i = 0; i < 8; ++i) {
@@ -897,6 +997,7 @@ static gbd_status rkf_step(gbd_mesh* m, const float* mm, double h, cudaStream_t 
     a.m0 = mm;
     a.kout = k[i];
     a.nk = i;
+    a.hdev = hdev;
     for (int j = 0; j < i; ++j) a.kin[j] = k[j];
     a.hrec = (extrap && i == 0) ? m->rk_hist + (size_t)m->rk_pend * n3 : nullptr;
     a.extrap = 0;
@@ -917,7 +1018,7 @@ static gbd_status rkf_step(gbd_mesh* m, const float* mm, double h, cudaStream_t 
       }
     }
     if (i < 7) {
-      for (int j = 0; j <= i; ++j) a.kw[j] = (float)(h * kRkfA[i + 1][j]);
+      for (int j = 0; j <= i; ++j) a.kw[j] = (float)(hk * kRkfA[i + 1][j]);
       a.mnext = stage_in[i % 2];
     } else {
       a.mnext = nullptr;
@@ -928,7 +1029,7 @@ static gbd_status rkf_step(gbd_mesh* m, const float* mm, double h, cudaStream_t 
       timed(m, GBD_PASS_EXTRAP, st, [&] { gbd::launch_extrap_stage(a, st); });
     } else {
       enqueue_conv(m, st);
-      timed(m, GBD_PASS_ROW_RK, st, [&] { gbd::launch_row(m->p.Lx, m->p.var_row, m->p.prec, a, m->tw, st); });
+      timed(m, GBD_PASS_ROW_RK, st, [&] { gbd::launch_row(m->p.Lx, row_var(m, a.mode), m->p.prec, a, m->tw, st); });
     }
     ms = a.mnext;
   }
@@ -938,21 +1039,109 @@ static gbd_status rkf_step(gbd_mesh* m, const float* mm, double h, cudaStream_t 
   f.m = mm;
   for (int i = 0; i < 8; ++i) {
     f.k[i] = k[i];
-    f.b5dt[i] = (float)(h * kRkfB5[i]);
+    f.b5dt[i] = (float)(hk * kRkfB5[i]);
     f.db[i] = (float)(kRkfB6[i] - kRkfB5[i]);
   }
   f.out = m->rk_m;
-  f.err_max = m->rk_err;
+  f.err_max = err_word;
+  f.hdev = hdev;
+  gbd::launch_rkf_final(f, st);
+}
+
+// One RKF5(6) step of size h from mm: the normalized fifth-order result into m->rk_m and the
+// error estimate h max_cells |sum_i (b6_i - b5_i) k_i| into *err (waits for the stream).
+static gbd_status rkf_step(gbd_mesh* m, const float* mm, double h, cudaStream_t st, double* err, bool extrap) {
   cudaError_t e = cudaMemsetAsync(m->rk_err, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return cuda_fail(e, "RKF5(6) step");
-  gbd::launch_rkf_final(f, st);
-  e = cudaMemcpyAsync(m->rk_err_host, m->rk_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  rkf_enqueue_attempt(m, mm, h, nullptr, m->rk_err, st, extrap);
+  unsigned err_word = 0;
+  e = cudaMemcpyAsync(&err_word, m->rk_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "RKF5(6) step");
   float ef;
-  std::memcpy(&ef, m->rk_err_host, sizeof(float));
+  std::memcpy(&ef, &err_word, sizeof(float));
   *err = h * (double)ef;
   return GBD_OK;
+}
+
+// gbd_llg_run_rkf56 without extrapolation: the whole adaptive run as one CUDA graph whose
+// conditional WHILE node repeats [attempt, step control, copy if accepted] until t_end or
+// max_steps, so the host neither waits nor launches between steps. The instantiated graph is
+// kept in the mesh for the magnetization array it was built on (and rebuilt after a parameter
+// or tuning change).
+static gbd_status rkf_run_device(gbd_mesh* m, float* mm, double t_end, double* dt, double tol, int max_steps,
+                                 int* accepted, int* rejected, cudaStream_t st) {
+  if (!m->rk_ctl) {
+    cudaError_t e = mesh_alloc(m->device, (void**)&m->rk_ctl, sizeof(gbd::RkfCtl));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      m->rk_ctl = nullptr;
+      return fail(e == cudaErrorMemoryAllocation ? GBD_ENOMEM : GBD_ECUDA, "RKF5(6) control block allocation");
+    }
+  }
+  if (!m->rkf_exec || m->rkf_key_m != mm || m->rkf_key_version != m->version) {
+    if (m->rkf_exec) {
+      cudaGraphExecDestroy(m->rkf_exec);
+      m->rkf_exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaGraphConditionalHandle cond;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        const int tmp = m->timing;
+        m->timing = 0;   // no timing events inside the graph
+        rkf_enqueue_attempt(m, mm, 0.0, &m->rk_ctl->hf, &m->rk_ctl->err, cs, false);
+        m->timing = tmp;
+        gbd::launch_rkf_control(m->rk_ctl, cond, kRkfSafety, kRkfFacMin, kRkfFacMax, cs);
+        gbd::launch_rkf_accept(m->rk_ctl, m->rk_m, mm, 3 * m->p.N, cs);
+        e = cudaStreamEndCapture(cs, &body);
+      }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&m->rkf_exec, g, 0);
+    if (cs) cudaStreamDestroy(cs);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      m->rkf_exec = nullptr;
+      return cuda_fail(e, "gbd_llg_run_rkf56: graph");
+    }
+    m->rkf_key_m = mm;
+    m->rkf_key_version = m->version;
+  }
+  gbd::RkfCtl c;
+  std::memset(&c, 0, sizeof(c));
+  c.t_end = t_end;
+  c.tol = tol;
+  c.h = std::min(*dt, t_end);
+  c.h_next = *dt;
+  c.hf = (float)c.h;
+  c.max_steps = max_steps;
+  cudaError_t e = cudaSuccess;
+  if (t_end > 0.0) {
+    e = cudaMemcpyAsync(m->rk_ctl, &c, sizeof(c), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaGraphLaunch(m->rkf_exec, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&c, m->rk_ctl, sizeof(c), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "gbd_llg_run_rkf56");
+  *dt = c.h_next;
+  if (accepted) *accepted = c.acc;
+  if (rejected) *rejected = c.rej;
+  mark_done(m, st);
+  return after_launch("gbd_llg_run_rkf56");
 }
 
 // Validates RKF flags, allocates what they need and resets the history unless continued.
@@ -982,6 +1171,7 @@ gbd_status gbd_llg_rkf56_step(gbd_mesh* m, float* mm, double dt, double* err, un
   rkf_accept(m, dt, extrap);
   cudaError_t e = cudaMemcpyAsync(mm, m->rk_m, (size_t)3 * m->p.N * sizeof(float), cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "gbd_llg_rkf56_step");
+  mark_done(m, st);
   return after_launch("gbd_llg_rkf56_step");
 }
 
@@ -998,6 +1188,7 @@ gbd_status gbd_llg_run_rkf56(gbd_mesh* m, float* mm, double t_end, double* dt, d
   if (s != GBD_OK) return s;
   const bool extrap = (flags & GBD_STEP_EXTRAP) != 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!extrap && !m->timing) return rkf_run_device(m, mm, t_end, dt, tol, max_steps, accepted, rejected, st);
   const size_t bytes = (size_t)3 * m->p.N * sizeof(float);
   double t = 0.0, h_next = *dt;
   int acc = 0, rej = 0;
@@ -1022,6 +1213,7 @@ gbd_status gbd_llg_run_rkf56(gbd_mesh* m, float* mm, double t_end, double* dt, d
   *dt = h_next;
   if (accepted) *accepted = acc;
   if (rejected) *rejected = rej;
+  mark_done(m, st);
   return after_launch("gbd_llg_run_rkf56");
 }
 
@@ -1031,17 +1223,19 @@ gbd_status gbd_llg_step(gbd_mesh* m, float* mm, int nsteps, double dt, void* str
 
 // ---- integrator state (checkpoint / resume) ---------------------------------------------------
 // Host image: a fixed header, then the RK4 demag history (5 slots of [3][N] float32) if the
-// mesh has one, then the RKF5(6) history (6 slots) if it has one.
+// mesh has one, then the RKF5(6) history (6 slots) if it has one. The header records the mesh
+// shape and periodic axes, so an image only loads into a mesh whose slots have its layout.
 struct StateHeader {
-  char magic[8];            // "GBDSTAT1"
+  char magic[8];            // "GBDSTAT2"
   long long N;              // cells
+  int nx, ny, nz, per;      // mesh shape and periodic axes of the saved mesh
   int has_hist, hist_count, hist_head, has_rk;
   double hist_dt;
   int rk_ring[5];
   int rk_count, rk_pend;
   double rk_ring_t[5];
 };
-static const char kStateMagic[8] = {'G', 'B', 'D', 'S', 'T', 'A', 'T', '1'};
+static const char kStateMagic[8] = {'G', 'B', 'D', 'S', 'T', 'A', 'T', '2'};
 
 static size_t state_bytes(const gbd_mesh* m) {
   const size_t slot = (size_t)3 * m->p.N * sizeof(float);
@@ -1063,6 +1257,10 @@ gbd_status gbd_mesh_get_state(gbd_mesh* m, void* host, size_t bytes, void* strea
   std::memset(&h, 0, sizeof(h));
   std::memcpy(h.magic, kStateMagic, sizeof(kStateMagic));
   h.N = m->p.N;
+  h.nx = m->p.nx;
+  h.ny = m->p.ny;
+  h.nz = m->p.nz;
+  h.per = m->p.per;
   h.has_hist = m->hist != nullptr;
   h.hist_count = m->hist_count;
   h.hist_head = m->hist_head;
@@ -1098,9 +1296,10 @@ gbd_status gbd_mesh_set_state(gbd_mesh* m, const void* host, size_t bytes, void*
   const size_t slot = (size_t)3 * m->p.N * sizeof(float);
   const bool ring_ok = h.rk_count >= 0 && h.rk_count <= 5 && h.rk_pend >= 0 && h.rk_pend < 6 &&
                        std::all_of(h.rk_ring, h.rk_ring + 5, [](int v) { return v >= 0 && v < 6; });
-  if (std::memcmp(h.magic, kStateMagic, sizeof(kStateMagic)) != 0 || h.N != m->p.N || h.hist_count < 0 ||
-      h.hist_count > 5 || h.hist_head < 0 || h.hist_head >= 5 || !ring_ok)
-    return fail(GBD_EINVAL, "not a state image of a mesh with this many cells");
+  if (std::memcmp(h.magic, kStateMagic, sizeof(kStateMagic)) != 0 || h.N != m->p.N || h.nx != m->p.nx ||
+      h.ny != m->p.ny || h.nz != m->p.nz || h.per != m->p.per || h.hist_count < 0 || h.hist_count > 5 ||
+      h.hist_head < 0 || h.hist_head >= 5 || !ring_ok)
+    return fail(GBD_EINVAL, "not a state image of a mesh of this shape and periodicity");
   if (bytes != sizeof(h) + (h.has_hist ? 5 * slot : 0) + (h.has_rk ? 6 * slot : 0))
     return fail(GBD_EINVAL, "state image size does not match its header");
   if (h.has_hist && (s = ensure_history(m)) != GBD_OK) return s;
@@ -1112,7 +1311,13 @@ gbd_status gbd_mesh_set_state(gbd_mesh* m, const void* host, size_t bytes, void*
     in += 5 * slot;
   }
   if (e == cudaSuccess && h.has_rk) e = cudaMemcpy(m->rk_hist, in, 6 * slot, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(e, "gbd_mesh_set_state");
+  if (e != cudaSuccess) {
+    // the device histories may be partly overwritten: the next extrapolated step restarts them
+    m->hist_count = 0;
+    m->rk_count = 0;
+    ++m->version;
+    return cuda_fail(e, "gbd_mesh_set_state");
+  }
   m->hist_count = h.has_hist ? h.hist_count : 0;
   m->hist_head = h.hist_head;
   m->hist_dt = h.hist_dt;
@@ -1205,13 +1410,14 @@ extern "C" gbd_status gbd_demag_noalloc(gbd_mesh* m, const float* M, float* H, v
   a.in = M;
   a.mode = gbd::ROW_FWD;
   a.fwd_after = 1;
-  gbd::launch_row(p.Lx, p.var_row, p.prec, a, m->tw, st);
+  gbd::launch_row(p.Lx, row_var(m, a.mode), p.prec, a, m->tw, st);
   enqueue_conv_on(m, S, T, st);
   a.hscale = 1.f;
   a.out = H;
   a.mode = gbd::ROW_H;
   a.fwd_after = 0;
-  gbd::launch_row(p.Lx, p.var_row, p.prec, a, m->tw, st);
+  gbd::launch_row(p.Lx, row_var(m, a.mode), p.prec, a, m->tw, st);
+  mark_done(m, st);
   return after_launch("gbd_demag_noalloc");
 }
 
@@ -1222,12 +1428,17 @@ extern "C" gbd_status gbd_demag_noalloc(gbd_mesh* m, const float* M, float* H, v
 // are grouped into blocks -- so the choice only changes speed. gbd_mesh_autotune times both
 // shapes of each pass the mesh uses, on the mesh's own (zeroed) buffers, keeps the faster one,
 // and caches the choice by mesh size and device: in the process, and in the text file named
-// by GBD_AUTOTUNE_CACHE when that is set (lines "nx ny nz device var_row var_film var_y var_z").
+// by GBD_AUTOTUNE_CACHE when that is set (lines "nx ny nz device Px Py precision var_row var_film
+// var_y var_z pow2 var_row_io"). For a mesh planned with 3 * 2^k / 5 * 2^k lengths it also times the
+// power-of-two plan of the same mesh and moves the mesh onto it when that is faster (pow2 = 1).
 
 namespace {
 struct TuneKey {
-  int nx, ny, nz, dev;
+  int nx, ny, nz, dev, Px, Py, prec;
   bool operator<(const TuneKey& o) const {
+    if (Px != o.Px) return Px < o.Px;
+    if (Py != o.Py) return Py < o.Py;
+    if (prec != o.prec) return prec < o.prec;
     if (nx != o.nx) return nx < o.nx;
     if (ny != o.ny) return ny < o.ny;
     if (nz != o.nz) return nz < o.nz;
@@ -1235,7 +1446,7 @@ struct TuneKey {
   }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::array<int, 4>> g_tune;
+std::map<TuneKey, std::array<int, 6>> g_tune;   // variants (row, film, y, z), power-of-two padding, row (transforms only)
 bool g_tune_file_read = false;
 
 const char* tune_file() {
@@ -1251,27 +1462,31 @@ void read_tune_file_locked() {
   FILE* f = std::fopen(path, "r");
   if (!f) return;
   TuneKey k;
-  std::array<int, 4> v;
-  while (std::fscanf(f, "%d %d %d %d %d %d %d %d", &k.nx, &k.ny, &k.nz, &k.dev, &v[0], &v[1], &v[2], &v[3]) == 8) {
-    bool ok = true;
-    for (int x : v) ok = ok && (x == 0 || x == 1);
+  std::array<int, 6> v;
+  while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d", &k.nx, &k.ny, &k.nz, &k.dev, &k.Px, &k.Py, &k.prec,
+                     &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]) == 13) {
+    bool ok = (v[4] == 0 || v[4] == 1) && v[5] >= 0 && v[5] <= 2;
+    for (int i = 0; i < 4; ++i) ok = ok && (v[i] == 0 || v[i] == 1 || (i == 0 && v[i] == 2));
     if (ok) g_tune[k] = v;
   }
   std::fclose(f);
 }
 
-void append_tune_file_locked(const TuneKey& k, const std::array<int, 4>& v) {
+void append_tune_file_locked(const TuneKey& k, const std::array<int, 6>& v) {
   const char* path = tune_file();
   if (!path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%d %d %d %d %d %d %d %d\n", k.nx, k.ny, k.nz, k.dev, v[0], v[1], v[2], v[3]);
+  std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d\n", k.nx, k.ny, k.nz, k.dev, k.Px, k.Py, k.prec, v[0], v[1],
+               v[2], v[3], v[4], v[5]);
   std::fclose(f);
 }
 
-void apply_tuning(gbd_mesh* m, const std::array<int, 4>& v) {
+template <class A>
+void apply_tuning(gbd_mesh* m, const A& v) {
   gbd::Plan& p = m->p;
   p.var_row = v[0];
+  p.var_row_io = v.size() > 5 ? v[5] : v[0];
   p.var_film = v[1];
   p.var_y = v[2];
   p.var_z = v[3];
@@ -1309,6 +1524,91 @@ cudaError_t time_variant(cudaStream_t st, int reps, F f, float* ms) {
 }
 }  // namespace
 
+namespace {
+// The mesh is planned with a 3 * 2^k or 5 * 2^k length that a power-of-two plan would replace.
+bool can_pad_pow2(const gbd_mesh* m) {
+  return m->p.prec == 0 && !(m->d.flags & GBD_FLAG_POW2_PAD) && (gbd::mixed_len(m->p.Lx) || gbd::mixed_len(m->p.Py));
+}
+
+// Mean device time of one demag evaluation's passes (forward x, convolution, inverse x) on the
+// mesh's own buffers (zeroed by the caller).
+cudaError_t time_demag_passes(gbd_mesh* m, cudaStream_t st, float* ms) {
+  gbd::RowArgs a = row_args(m);
+  return time_variant(st, 5, [&] {
+    a.in = m->bufA;
+    a.mode = gbd::ROW_FWD;
+    a.fwd_after = 1;
+    gbd::launch_row(m->p.Lx, row_var(m, a.mode), m->p.prec, a, m->tw, st);
+    enqueue_conv(m, st);
+    a.out = m->bufB;
+    a.mode = gbd::ROW_H;
+    a.fwd_after = 0;
+    gbd::launch_row(m->p.Lx, row_var(m, a.mode), m->p.prec, a, m->tw, st);
+  }, ms);
+}
+
+// A scratch copy of m planned on powers of two (kernel spectrum zero: for timing only), tuned.
+gbd_status make_pow2_twin(gbd_mesh* m, void* stream, gbd_mesh** out) {
+  gbd_mesh_desc d2 = m->d;
+  d2.flags |= GBD_FLAG_POW2_PAD;
+  gbd_status s = gbd_mesh_create(&d2, out);
+  if (s != GBD_OK) return s;
+  gbd_mesh* t = *out;
+  cudaError_t e = cudaMemsetAsync(t->K, 0, t->p.bytes_K, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    gbd_mesh_destroy(t);
+    return cuda_fail(e, "gbd_mesh_autotune: power-of-two plan");
+  }
+  t->kernel_set = true;
+  s = gbd_mesh_autotune(t, stream);
+  if (s != GBD_OK) gbd_mesh_destroy(t);
+  return s;
+}
+
+gbd_status pow2_is_faster(gbd_mesh* m, void* stream, int* pow2) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  gbd_mesh* twin = nullptr;
+  gbd_status s = make_pow2_twin(m, stream, &twin);
+  if (s != GBD_OK) return s;
+  float t_cur = 0.f, t_pow2 = 0.f;
+  cudaError_t e = time_demag_passes(m, st, &t_cur);
+  if (e == cudaSuccess) e = time_demag_passes(twin, st, &t_pow2);
+  gbd_mesh_destroy(twin);
+  if (e != cudaSuccess) return cuda_fail(e, "gbd_mesh_autotune: padded length");
+  *pow2 = t_pow2 < 0.98f * t_cur ? 1 : 0;   // keep the shorter lengths unless clearly slower
+  return GBD_OK;
+}
+
+// Moves m onto its power-of-two plan: new spectrum buffers and twiddles from a tuned twin, the
+// kernel spectrum recomputed for the new lengths; the old buffers are freed after m's work.
+gbd_status move_to_pow2(gbd_mesh* m, void* stream) {
+  gbd_mesh* twin = nullptr;
+  gbd_status s = make_pow2_twin(m, stream, &twin);
+  if (s != GBD_OK) return s;
+  for (auto& d : m->done) cudaEventSynchronize(d.second);
+  std::swap(m->p, twin->p);
+  std::swap(m->S, twin->S);
+  std::swap(m->T, twin->T);
+  std::swap(m->K, twin->K);
+  std::swap(m->tw, twin->tw);
+  m->d.flags |= GBD_FLAG_POW2_PAD;
+  ++m->version;
+  gbd_mesh_destroy(twin);
+  return gbd_set_kernel(m, stream);
+}
+}  // namespace
+
+extern "C" gbd_status gbd_mesh_plan_dims(const gbd_mesh* m, int out[6]) {
+  if (!m || !out) return fail(GBD_EINVAL, "NULL argument");
+  out[0] = m->p.Px;
+  out[1] = m->p.Py;
+  out[2] = m->p.Pz;
+  out[3] = m->p.Hx;
+  out[4] = m->p.Ky;
+  out[5] = m->p.Kz;
+  return GBD_OK;
+}
+
 extern "C" gbd_status gbd_mesh_get_tuning(const gbd_mesh* m, int out[4]) {
   if (!m || !out) return fail(GBD_EINVAL, "NULL argument");
   out[0] = m->p.var_row;
@@ -1322,7 +1622,8 @@ extern "C" gbd_status gbd_mesh_set_tuning(gbd_mesh* m, const int in[4]) {
   if (!m || !in) return fail(GBD_EINVAL, "NULL argument");
   std::array<int, 4> v;
   for (int i = 0; i < 4; ++i) {
-    if (in[i] != 0 && in[i] != 1) return fail(GBD_EINVAL, "tile variants are 0 or 1");
+    if (in[i] != 0 && in[i] != 1 && !(i == 0 && in[i] == 2))
+      return fail(GBD_EINVAL, "tile variants are 0 or 1 (row: 0, 1 or 2)");
     v[i] = in[i];
   }
   apply_tuning(m, v);
@@ -1333,13 +1634,16 @@ extern "C" gbd_status gbd_mesh_autotune(gbd_mesh* m, void* stream) {
   gbd_status s = ready(m);
   if (s != GBD_OK) return s;
   const gbd::Plan& p = m->p;
-  const TuneKey key{p.nx, p.ny, p.nz, m->device};
+  const TuneKey key{p.nx, p.ny, p.nz, m->device, p.Px, p.Py, p.prec};
   {
-    std::lock_guard<std::mutex> lock(g_tune_mu);
+    std::unique_lock<std::mutex> lock(g_tune_mu);
     read_tune_file_locked();
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      apply_tuning(m, it->second);
+      const std::array<int, 6> v = it->second;
+      lock.unlock();
+      apply_tuning(m, v);
+      if (v[4] == 1 && can_pad_pow2(m)) return move_to_pow2(m, stream);
       return GBD_OK;
     }
   }
@@ -1354,15 +1658,18 @@ extern "C" gbd_status gbd_mesh_autotune(gbd_mesh* m, void* stream) {
   if (e != cudaSuccess) return cuda_fail(e, "gbd_mesh_autotune: memset");
   const int reps = 5;
   std::array<int, 4> best = {p.var_row, p.var_film, p.var_y, p.var_z};
-  auto pick = [&](int slot, auto launch_v) -> cudaError_t {
-    float t[2];
-    for (int v = 0; v < 2; ++v) {
+  auto pick = [&](int slot, auto launch_v, int nvar = 2) -> cudaError_t {
+    float t[3];
+    for (int v = 0; v < nvar; ++v) {
       cudaError_t ee = time_variant(st, reps, [&] { launch_v(v); }, &t[v]);
       if (ee != cudaSuccess) return ee;
     }
-    // keep the default unless the other shape is faster by more than 2 %
+    // keep the default unless another shape is faster by more than 2 %
     const int def = best[slot];
-    best[slot] = (t[1 - def] < 0.98f * t[def]) ? 1 - def : def;
+    int b = def;
+    for (int v = 0; v < nvar; ++v)
+      if (t[v] < 0.98f * t[def] && t[v] < t[b]) b = v;
+    best[slot] = b;
     return cudaSuccess;
   };
   // x rows: an RK4 middle stage with the next forward transform, on zeroed state
@@ -1374,7 +1681,30 @@ extern "C" gbd_status gbd_mesh_autotune(gbd_mesh* m, void* stream) {
   ra.acc = m->acc;
   ra.mode = gbd::ROW_RK2;
   ra.fwd_after = 1;
-  e = pick(0, [&](int v) { gbd::launch_row(p.Lx, v, p.prec, ra, m->tw, st); });
+  e = pick(0, [&](int v) { gbd::launch_row(p.Lx, v, p.prec, ra, m->tw, st); }, p.prec == 0 ? 3 : 2);
+  // the transform-only x-row launches: a forward transform and an inverse one to H_d
+  int best_io = p.var_row_io;
+  if (e == cudaSuccess) {
+    gbd::RowArgs fa = row_args(m), ia = row_args(m);
+    fa.in = m->bufA;
+    fa.mode = gbd::ROW_FWD;
+    fa.fwd_after = 1;
+    ia.out = m->bufB;
+    ia.mode = gbd::ROW_H;
+    float t[3];
+    const int nv = p.prec == 0 ? 3 : 2;
+    for (int v = 0; v < nv && e == cudaSuccess; ++v)
+      e = time_variant(st, reps, [&] {
+        gbd::launch_row(p.Lx, v, p.prec, fa, m->tw, st);
+        gbd::launch_row(p.Lx, v, p.prec, ia, m->tw, st);
+      }, &t[v]);
+    if (e == cudaSuccess) {
+      int b = best_io;
+      for (int v = 0; v < nv; ++v)
+        if (t[v] < 0.98f * t[best_io] && t[v] < t[b]) b = v;
+      best_io = b;
+    }
+  }
   gbd::ColArgs ca = col_args(m);
   if (e == cudaSuccess && p.film) {
     ca.dst = m->S;
@@ -1404,13 +1734,22 @@ extern "C" gbd_status gbd_mesh_autotune(gbd_mesh* m, void* stream) {
     if (e == cudaSuccess) e = pick(3, [&](int v) { gbd::launch_z_conv(v, p.prec, ca, m->tw, st); });
   }
   if (e != cudaSuccess) return cuda_fail(e, "gbd_mesh_autotune");
-  apply_tuning(m, best);
-  std::lock_guard<std::mutex> lock(g_tune_mu);
-  if (g_tune.find(key) == g_tune.end()) {
-    g_tune[key] = best;
-    append_tune_file_locked(key, best);
+  apply_tuning(m, std::array<int, 6>{best[0], best[1], best[2], best[3], 0, best_io});
+  // padded length: against the same mesh on power-of-two lengths
+  int pow2 = 0;
+  if (can_pad_pow2(m)) {
+    s = pow2_is_faster(m, stream, &pow2);
+    if (s != GBD_OK) return s;
   }
-  return GBD_OK;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    if (g_tune.find(key) == g_tune.end()) {
+      const std::array<int, 6> v = {best[0], best[1], best[2], best[3], pow2, best_io};
+      g_tune[key] = v;
+      append_tune_file_locked(key, v);
+    }
+  }
+  return pow2 ? move_to_pow2(m, stream) : GBD_OK;
 }
 
 // ---- batched meshes: one CUDA graph per run ------------------------------------------------
@@ -1590,6 +1929,7 @@ extern "C" gbd_status gbd_batch_run_ex(gbd_batch* b, float* const* m, const int*
   if (e != cudaSuccess) return cuda_fail(e, "gbd_batch_run: graph launch");
   cudaEventRecord(b->ev_out, og);
   cudaStreamWaitEvent(st, b->ev_out, 0);
+  for (gbd_mesh* mesh : b->meshes) mark_done(mesh, og);
   return after_launch("gbd_batch_run");
 }
 
@@ -1599,7 +1939,9 @@ extern "C" gbd_status gbd_batch_run(gbd_batch* b, float* const* m, const int* ns
 
 extern "C" gbd_status gbd_batch_destroy(gbd_batch* b) {
   if (!b) return GBD_OK;
-  if (b->device >= 0) cudaDeviceSynchronize();
+  // the batch's last graph launch must have finished before its executable graph goes; the
+  // rest of the device keeps running
+  if (b->ev_out) cudaEventSynchronize(b->ev_out);
   destroy_batch(b);
   return GBD_OK;
 }

@@ -21,9 +21,13 @@ static bool z_dispatch(int Pz, int var, int prec, const ColArgs* a, const float2
 }
 
 bool launch_film_conv(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st) {
+  if (mixed_len(a.Py)) return prec == 0 && film_dispatch_mixed(a.Py, &a, tw, st);
   return film_dispatch(a.Py, var, prec, &a, tw, st);
 }
-bool prepare_film_conv(int Py, int prec) { return film_dispatch(Py, -1, prec, nullptr, nullptr, nullptr); }
+bool prepare_film_conv(int Py, int prec) {
+  if (mixed_len(Py)) return prec <= 0 && film_dispatch_mixed(Py, nullptr, nullptr, nullptr);
+  return film_dispatch(Py, -1, prec, nullptr, nullptr, nullptr);
+}
 
 bool launch_z_conv(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st) {
   return z_dispatch(a.Pz, var, prec, &a, tw, st);

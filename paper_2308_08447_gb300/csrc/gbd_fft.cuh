@@ -22,11 +22,18 @@
 // Shared memory rows are padded: element i of a line sits at i + i/16, which makes the
 // stride-16 accesses of the Ns = 1 pass and its adjoint conflict free.
 //
-// Twiddles come from one table of all power-of-two levels, written on the host in FP64 and
-// rounded to FP32: level N (1 <= N <= GBD_TW_LEN) holds E_N[m] = exp(-2 pi i m / N),
-// m in [0, N), at index N + m. A butterfly of a pass (Ns, R) at position k loads
-// w^r = E_(Ns R / r)[k] for r = 1, 2, 4, 8, so the lanes of a warp, which hold consecutive
-// k, read consecutive entries; it forms the other powers with at most three complex products.
+// Twiddles come from one table of levels, written on the host in FP64 and rounded to FP32:
+// level N holds E_N[m] = exp(-2 pi i m / N), m in [0, N), at index tw_base(N) + m, for the
+// powers of two N <= GBD_TW_LEN and for N = 3 * 2^j and 5 * 2^j up to the largest padded
+// length. A butterfly of a pass (Ns, R) at position k loads w^r = E_(Ns R / r)[k] for
+// r = 1, 2, 4, 8, so the lanes of a warp, which hold consecutive k, read consecutive entries;
+// it forms the other powers with at most three complex products.
+//
+// Lengths. L = r 2^k with r in {1, 3, 5}. For r > 1 the first forward pass (Ns = 1, no
+// twiddles) is a radix-r pass and the power-of-two passes follow with Ns = r, 16 r, ...; a
+// thread then runs ceil(16 / r) radix-r butterflies of that pass (the last ones of the block
+// may be past the end and are skipped). This lets the zero padding of Sec. II stop at the
+// smallest such length >= 2n - 1 instead of the next power of two.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -36,6 +43,13 @@
 // DFT-16 fragments (gbd_tc.cuh): 4 tables (sign x 16-bit type) of 32 registers x 32 lanes of
 // 32 bits, i.e. 2048 float2 slots.
 #define GBD_TC_FRAG_F2 2048
+// Then the levels 3 * 2^j (up to 6144) and 5 * 2^j (up to 5120): level N of odd part r starts
+// at its region's offset + N - r (the levels r, 2r, 4r, ... are stored back to back).
+#define GBD_TW3_OFF (2 * GBD_TW_LEN + GBD_TC_FRAG_F2)
+#define GBD_TW3_MAX 6144
+#define GBD_TW5_OFF (GBD_TW3_OFF + 2 * GBD_TW3_MAX)
+#define GBD_TW5_MAX 5120
+#define GBD_TW_TOTAL (GBD_TW5_OFF + 2 * GBD_TW5_MAX)
 
 namespace gbd {
 
@@ -51,10 +65,17 @@ __device__ __forceinline__ float2 cmul_i(float2 a) {  // a * (S i)
   return S > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
-// exp(S 2 pi i m / N) for a power of two N <= GBD_TW_LEN and 0 <= m < N
+// L over its largest power-of-two factor (no recursion, so that it folds wherever L is known)
+__host__ __device__ constexpr int odd_part(int L) { return L > 0 ? L / (L & -L) : L; }
+// index of E_N[0] in the twiddle table (N = 2^j, 3 * 2^j or 5 * 2^j)
+__host__ __device__ constexpr int tw_base(int N) {
+  return odd_part(N) == 1 ? N : odd_part(N) == 3 ? GBD_TW3_OFF + N - 3 : GBD_TW5_OFF + N - 5;
+}
+
+// exp(S 2 pi i m / N) for a level N of the table and 0 <= m < N
 template <int S>
 __device__ __forceinline__ float2 twiddle_at(const float2* __restrict__ tw, int N, int m) {
-  float2 w = __ldg(tw + N + m);
+  float2 w = __ldg(tw + tw_base(N) + m);
   return S < 0 ? w : cconj(w);
 }
 // exp(S 2 pi i m / GBD_TW_LEN) for any m
@@ -66,15 +87,15 @@ __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int m) 
 // ---- radix decomposition (compile time) -------------------------------------------------
 __host__ __device__ constexpr int ilog2(int L) { return L <= 1 ? 0 : 1 + ilog2(L / 2); }
 
-// Passes of radix 16 and one remainder. With CONV the last radix is at most 8 (the
-// convolution kernels keep three components of that pass in registers).
-__host__ __device__ constexpr int npasses(int L, bool conv) {
+// Power-of-two lengths: passes of radix 16 and one remainder. With CONV the last radix is at
+// most 8 (the convolution kernels keep three components of that pass in registers).
+__host__ __device__ constexpr int npasses2(int L, bool conv) {
   return ilog2(L) == 0 ? 0
          : ilog2(L) % 4 == 0 ? (conv ? ilog2(L) / 4 + 1 : ilog2(L) / 4)
          : ilog2(L) % 4 == 3 ? ilog2(L) / 4 + 1
          : (ilog2(L) <= 2 ? 1 : ilog2(L) / 4 + 1);
 }
-__host__ __device__ constexpr int radix_at(int L, bool conv, int p) {
+__host__ __device__ constexpr int radix_at2(int L, bool conv, int p) {
   // sequence: 16 ... 16, then the tail
   return ilog2(L) % 4 == 0
              ? (conv ? (p < ilog2(L) / 4 - 1 ? 16 : (p == ilog2(L) / 4 - 1 ? 2 : 8)) : 16)
@@ -83,6 +104,13 @@ __host__ __device__ constexpr int radix_at(int L, bool conv, int p) {
          : ilog2(L) == 2 ? 4
          : ilog2(L) % 4 == 1 ? (p < (ilog2(L) - 5) / 4 ? 16 : (p == (ilog2(L) - 5) / 4 ? 4 : 8))
                              : (p < (ilog2(L) - 6) / 4 ? 16 : 8);
+}
+// Any length r 2^k: a radix-r pass first when r > 1, then the power-of-two passes of 2^k.
+__host__ __device__ constexpr int npasses(int L, bool conv) {
+  return odd_part(L) > 1 ? 1 + npasses2(L / odd_part(L), conv) : npasses2(L, conv);
+}
+__host__ __device__ constexpr int radix_at(int L, bool conv, int p) {
+  return odd_part(L) > 1 ? (p == 0 ? odd_part(L) : radix_at2(L / odd_part(L), conv, p - 1)) : radix_at2(L, conv, p);
 }
 __host__ __device__ constexpr int ns_at(int L, bool conv, int p) {
   return p == 0 ? 1 : ns_at(L, conv, p - 1) * radix_at(L, conv, p - 1);
@@ -151,9 +179,46 @@ __device__ __forceinline__ void dft16(float2* x) {
   }
 }
 
+// DFT_3: X0 = x0 + x1 + x2, X1,2 = x0 - (x1 + x2)/2 +- S i (sqrt(3)/2)(x1 - x2)
+template <int S>
+__device__ __forceinline__ void dft3(float2* x) {
+  const float h = 0.86602540378443864676f;   // sin(2 pi / 3)
+  const float2 t1 = cadd(x[1], x[2]), t2 = csub(x[1], x[2]);
+  const float2 m = make_float2(fmaf(-0.5f, t1.x, x[0].x), fmaf(-0.5f, t1.y, x[0].y));
+  const float2 u = make_float2(-S * h * t2.y, S * h * t2.x);
+  x[0] = cadd(x[0], t1);
+  x[1] = cadd(m, u);
+  x[2] = csub(m, u);
+}
+
+// DFT_5 by the symmetric pairs a_n = x_n + x_(5-n), b_n = x_n - x_(5-n) (n = 1, 2), with
+// c_q = cos(2 pi q / 5), s_q = sin(2 pi q / 5):
+//   X_1,4 = x0 + c1 a1 + c2 a2 +- S i (s1 b1 + s2 b2),  X_2,3 = x0 + c2 a1 + c1 a2 +- S i (s2 b1 - s1 b2)
+template <int S>
+__device__ __forceinline__ void dft5(float2* x) {
+  const float c1 = 0.30901699437494742410f, c2 = -0.80901699437494742410f;
+  const float s1 = 0.95105651629515357212f, s2 = 0.58778525229247312917f;
+  const float2 a1 = cadd(x[1], x[4]), b1 = csub(x[1], x[4]);
+  const float2 a2 = cadd(x[2], x[3]), b2 = csub(x[2], x[3]);
+  const float2 p1 = make_float2(x[0].x + c1 * a1.x + c2 * a2.x, x[0].y + c1 * a1.y + c2 * a2.y);
+  const float2 p2 = make_float2(x[0].x + c2 * a1.x + c1 * a2.x, x[0].y + c2 * a1.y + c1 * a2.y);
+  const float2 q1 = make_float2(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y);   // times S i below
+  const float2 q2 = make_float2(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y);
+  const float2 u1 = make_float2(-S * q1.y, S * q1.x), u2 = make_float2(-S * q2.y, S * q2.x);
+  x[0] = cadd(x[0], cadd(a1, a2));
+  x[1] = cadd(p1, u1);
+  x[4] = csub(p1, u1);
+  x[2] = cadd(p2, u2);
+  x[3] = csub(p2, u2);
+}
+
 template <int R, int S>
 __device__ __forceinline__ void dft(float2* x) {
-  if constexpr (R == 2) {
+  if constexpr (R == 3) {
+    dft3<S>(x);
+  } else if constexpr (R == 5) {
+    dft5<S>(x);
+  } else if constexpr (R == 2) {
     float2 t = x[0];
     x[0] = cadd(t, x[1]);
     x[1] = csub(t, x[1]);
@@ -283,14 +348,17 @@ template <int S, bool ADJ, int L, int R, int Ns, int LINES, bool LF, bool SYNC_M
           class ST>
 __device__ __forceinline__ void stockham_pass(const float2* __restrict__ tw, LD ld, ST st) {
   static_assert(!HALF || Ns == 1, "the half transforms are the Ns = 1 pass");
+  static_assert(R % 2 == 0 || Ns == 1, "an odd radix is the Ns = 1 pass");
   constexpr int LR = L / R;
-  constexpr int NB = GBD_E / R;
+  constexpr int NB = (GBD_E + R - 1) / R;   // butterflies per thread (radix 3, 5: the last may be past the end)
   constexpr int T = LINES * L / GBD_E;
+  constexpr int NBUT = LINES * LR;
   float2 v[NB][R];
   int bl[NB], bj[NB];
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
     const int b = threadIdx.x + i * T;
+    if (NB * T != NBUT && b >= NBUT) continue;
     int line, j;
     if (LF) {
       line = b % LINES;
@@ -308,6 +376,7 @@ __device__ __forceinline__ void stockham_pass(const float2* __restrict__ tw, LD 
   if (SYNC_MID) __syncthreads();
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
+    if (NB * T != NBUT && threadIdx.x + i * T >= NBUT) continue;
     const int j = bj[i];
     const int k = j % Ns;
     if constexpr (HALF && ADJ)
@@ -330,9 +399,11 @@ __device__ __forceinline__ void stockham_pass(const float2* __restrict__ tw, LD 
 // (other cases compute pad per element).
 template <int S, bool ADJ, int L, int R, int Ns, int LINES, bool LF, int LS>
 __device__ __forceinline__ void stockham_pass_sm(float2* sm, const float2* __restrict__ tw) {
+  static_assert(R % 2 == 0 || Ns == 1, "an odd radix is the Ns = 1 pass");
   constexpr int LR = L / R;
-  constexpr int NB = GBD_E / R;
+  constexpr int NB = (GBD_E + R - 1) / R;
   constexpr int T = LINES * L / GBD_E;
+  constexpr int NBUT = LINES * LR;
   constexpr bool NAT_CONST = (LR % 16 == 0);
   constexpr bool SCA_CONST = (Ns % 16 == 0) || (Ns == 1 && R == 16);
   constexpr int NAT_STRIDE = LR + LR / 16;
@@ -342,6 +413,7 @@ __device__ __forceinline__ void stockham_pass_sm(float2* sm, const float2* __res
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
     const int b = threadIdx.x + i * T;
+    if (NB * T != NBUT && b >= NBUT) continue;
     int line, j;
     if (LF) {
       line = b % LINES;
@@ -364,6 +436,7 @@ __device__ __forceinline__ void stockham_pass_sm(float2* sm, const float2* __res
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < NB; ++i) {
+    if (NB * T != NBUT && threadIdx.x + i * T >= NBUT) continue;
     const int j = bj[i];
     const int k = j % Ns;
     butterfly<S, R, Ns, ADJ>(v[i], k, tw);

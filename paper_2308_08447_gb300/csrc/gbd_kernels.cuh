@@ -16,6 +16,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "gbd_fft.cuh"
+
 namespace gbd {
 
 // What the x-row kernel does after (or instead of) the inverse x transform.
@@ -34,17 +36,27 @@ enum RowMode : int {
 
 // Block shapes per transform length L and tile variant v, shared by host planning and the
 // kernels. Every kernel has 16 complex values per thread, so threads = lines * L / 16.
+// Lengths 3 * 2^k and 5 * 2^k (FP32 only) have one tile shape, sized from the largest power
+// of two below the length (576 or 480 threads per x-row block).
+__host__ __device__ constexpr int pow2_floor(int L) { return L < 2 ? 1 : 2 * pow2_floor(L / 2); }
+__host__ __device__ constexpr bool mixed_len(int L) { return L > 1 && odd_part(L) > 1; }
 // rows per x-row block (3 lines each): 2048 or 4096 complex values per component
 __host__ __device__ constexpr int row_rb(int Lx, int v) {
-  return v == 0 ? (Lx >= 2048 ? 1 : 2048 / Lx) : (Lx >= 4096 ? 1 : 4096 / Lx);
+  return mixed_len(Lx) ? (Lx >= 4096 ? 1 : (2048 / pow2_floor(Lx) > 0 ? 2048 / pow2_floor(Lx) : 1))
+         : v == 0      ? (Lx >= 2048 ? 1 : 2048 / Lx)
+                       : (Lx >= 4096 ? 1 : 4096 / Lx);
 }
 // kx columns per film-convolution block (3 lines each)
 __host__ __device__ constexpr int film_cols(int Py, int v) {
-  return v == 0 ? (Py >= 1024 ? 1 : 1024 / Py) : (Py >= 4096 ? 1 : 2 * (Py >= 1024 ? 1 : 1024 / Py));
+  return mixed_len(Py) ? (pow2_floor(Py) >= 1024 ? 1 : 1024 / pow2_floor(Py))
+         : v == 0      ? (Py >= 1024 ? 1 : 1024 / Py)
+                       : (Py >= 4096 ? 1 : 2 * (Py >= 1024 ? 1 : 1024 / Py));
 }
 // y lines per 3D y-pass block
 __host__ __device__ constexpr int ypass_lines(int Py, int v) {
-  return v == 0 ? (Py >= 4096 ? 1 : 4096 / Py) : (Py >= 2048 ? 1 : 2048 / Py);
+  return mixed_len(Py) ? (pow2_floor(Py) >= 4096 ? 1 : 4096 / pow2_floor(Py))
+         : v == 0      ? (Py >= 4096 ? 1 : 4096 / Py)
+                       : (Py >= 2048 ? 1 : 2048 / Py);
 }
 // (kx, ky) columns per z-convolution block (3 lines each)
 __host__ __device__ constexpr int zconv_cols(int Pz, int v) {
@@ -81,11 +93,13 @@ struct RowArgs {
   const float* hist[6];
   float* hrec;
   // general explicit RK stage (ROW_RKG): kin[0..nk) are earlier stages' dm/dt, kw their
-  // weights dt a_(i+1),j, kw[nk] the weight of this stage's k; mnext may be null (last stage)
+  // weights dt a_(i+1),j, kw[nk] the weight of this stage's k; mnext may be null (last stage).
+  // With hdev set the step size lives on the device: kw holds a_(i+1),j and is scaled by *hdev.
   float* kout;
   const float* kin[7];
   float kw[8];
   int nk;
+  const float* hdev;
 };
 
 // Final combination of an RKF5(6) step (Sec. III): m5 = normalize(m + sum_i b5dt[i] k_i) per
@@ -94,10 +108,24 @@ struct RkfArgs {
   long long N;
   const float* m;
   const float* k[8];
-  float b5dt[8];
+  float b5dt[8];            // dt b5 (or b5, scaled by *hdev when hdev is set)
   float db[8];
   float* out;
   unsigned* err_max;
+  const float* hdev;
+};
+
+// Device-side step control of an adaptive RKF5(6) run (Sec. III), one CUDA-graph loop for the
+// whole run: after each attempt the control kernel reads the attempt's error, accepts or rejects
+// it, picks the next step size and sets the loop's condition.
+struct RkfCtl {
+  double t, t_end, tol;     // time reached, end time, tolerance
+  double h;                 // step size of the next attempt (the last one is cut at t_end)
+  double h_next;            // the controller's proposal after the last attempt
+  unsigned err;             // largest error norm of the current attempt (float bits); reset after use
+  float hf;                 // h in FP32, read by the stage kernels
+  int acc, rej, max_steps;  // accepted and rejected attempts, attempt limit
+  int accepted;             // the last attempt was accepted
 };
 
 struct ColArgs {
@@ -120,6 +148,12 @@ bool launch_row(int Lx, int var, int prec, const RowArgs& a, const float2* tw, c
 // the row kernel's epilogue alone, at full occupancy.
 void launch_extrap_stage(const RowArgs& a, cudaStream_t st);
 void launch_rkf_final(const RkfArgs& a, cudaStream_t st);
+// One thread: the step controller of RkfCtl (safety factor, smallest and largest step ratios),
+// and cudaGraphSetConditional(cond, continue) for the enclosing graph loop.
+void launch_rkf_control(RkfCtl* c, cudaGraphConditionalHandle cond, double safety, double fac_min, double fac_max,
+                        cudaStream_t st);
+// dst = src over n floats when the last attempt was accepted.
+void launch_rkf_accept(const RkfCtl* c, const float* src, float* dst, long long n, cudaStream_t st);
 // Writes the split DFT-16 fragment tables of the tensor-core passes (gbd_tc.cuh) into the
 // GBD_TC_FRAG_F2 float2 slots at frag (the mesh's twiddle buffer after its levels).
 void launch_dft16_frags(float2* frag, cudaStream_t st);
@@ -127,6 +161,13 @@ bool launch_film_conv(int var, int prec, const ColArgs& a, const float2* tw, cud
 bool launch_y_fwd(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st);
 bool launch_y_inv(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st);
 bool launch_z_conv(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st);
+
+// Transform lengths 3 * 2^k and 5 * 2^k (FP32 only; gbd_mixed_row.cu, gbd_mixed_conv.cu):
+// the launchers above forward them here. a == nullptr prepares without launching. False for
+// a length without an instantiation.
+bool row_dispatch_mixed(int Lx, int var, const RowArgs* a, const float2* tw, cudaStream_t st);
+bool film_dispatch_mixed(int Py, const ColArgs* a, const float2* tw, cudaStream_t st);
+bool ypass_dispatch_mixed(int Py, bool inv, const ColArgs* a, const float2* tw, cudaStream_t st);
 
 // Set the kernels' shared-memory attribute for both variants of a length without launching
 // (done when a mesh is created, so later launches inside a stream capture need no driver

@@ -8,9 +8,22 @@
 #include <set>
 #include <utility>
 
-#include "gbd_row.cuh"
+#include "gbd_rowpipe.cuh"
 
 namespace gbd {
+
+int sm_count() {
+  static int count[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (count[dev] == 0) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    count[dev] = n > 0 ? n : 1;
+  }
+  return count[dev];
+}
 
 bool prep_seen(const void* k, int dev) {
   static std::mutex mu;
@@ -27,6 +40,7 @@ __global__ void __launch_bounds__(256) rkf_final_kernel(const RkfArgs a) {
   float e2 = 0.f;
   if (i < a.N) {
     float v[3], d[3];
+    const float hs = a.hdev ? *a.hdev : 1.f;   // step size on the device, or folded into b5dt
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       v[c] = a.m[c * a.N + i];
@@ -34,7 +48,7 @@ __global__ void __launch_bounds__(256) rkf_final_kernel(const RkfArgs a) {
 #pragma unroll
       for (int s = 0; s < 8; ++s) {
         const float ks = a.k[s][c * a.N + i];
-        v[c] = fmaf(a.b5dt[s], ks, v[c]);
+        v[c] = fmaf(a.b5dt[s] * hs, ks, v[c]);
         d[c] = fmaf(a.db[s], ks, d[c]);
       }
     }
@@ -107,10 +121,17 @@ static void set_vec8(RowArgs& a) {
   a.vec8 = ok ? 1 : 0;
 }
 
+// Tile variant 2 is the persistent pipelined kernel (gbd_rowpipe.cuh, FP32 only) where it
+// applies; other launches of variant 2 take row_kernel's variant 1.
 bool launch_row(int Lx, int var, int prec, const RowArgs& a0, const float2* tw, cudaStream_t st) {
   RowArgs a = a0;
   set_vec8(a);
-  return row_dispatch(Lx, var, prec, &a, tw, st);
+  if (mixed_len(Lx)) return prec == 0 && row_dispatch_mixed(Lx, var, &a, tw, st);
+  if (var == 2 && prec == 0) {
+    const int kind = pipe_kind(Lx, a);
+    if (kind >= 0) return pipe_dispatch(Lx, kind, &a, tw, st);
+  }
+  return row_dispatch(Lx, var == 2 ? 1 : var, prec, &a, tw, st);
 }
 
 // One warp: lane l writes register r of each table at word r * 32 + l (Dft16Frags::load).
@@ -141,12 +162,59 @@ void launch_rkf_final(const RkfArgs& a, cudaStream_t st) {
   rkf_final_kernel<<<(unsigned)((a.N + 255) / 256), 256, 0, st>>>(a);
 }
 
+// The host loop's rule on the device: err = h max|...| from the attempt's error word; accept when
+// err <= tol; next size h min(fac_max, max(fac_min, safety (tol / err)^(1/6))), the last step cut
+// at t_end; the loop goes on while t < t_end and fewer than max_steps attempts were made (so it
+// always ends: every pass counts an attempt).
+__global__ void rkf_control_kernel(RkfCtl* c, cudaGraphConditionalHandle cond, double safety, double fac_min,
+                                   double fac_max) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double h = c->h;
+  const double err = h * (double)__uint_as_float(c->err);
+  const double fac = err == 0.0 ? fac_max : fmin(fac_max, fmax(fac_min, safety * pow(c->tol / err, 1.0 / 6.0)));
+  const int ok = err <= c->tol;
+  if (ok) {
+    c->t += h;
+    c->acc += 1;
+  } else {
+    c->rej += 1;
+  }
+  c->accepted = ok;
+  c->err = 0u;
+  c->h_next = h * fac;
+  const double hn = fmin(c->h_next, c->t_end - c->t);
+  c->h = hn;
+  c->hf = (float)hn;
+  const bool go = c->t < c->t_end && c->acc + c->rej < c->max_steps && hn > 0.0;
+  cudaGraphSetConditional(cond, go ? 1u : 0u);
+}
+
+__global__ void __launch_bounds__(256) rkf_accept_kernel(const RkfCtl* c, const float* __restrict__ src,
+                                                         float* __restrict__ dst, long long n) {
+  if (!c->accepted) return;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i];
+}
+
+void launch_rkf_control(RkfCtl* c, cudaGraphConditionalHandle cond, double safety, double fac_min, double fac_max,
+                        cudaStream_t st) {
+  rkf_control_kernel<<<1, 32, 0, st>>>(c, cond, safety, fac_min, fac_max);
+}
+
+void launch_rkf_accept(const RkfCtl* c, const float* src, float* dst, long long n, cudaStream_t st) {
+  rkf_accept_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c, src, dst, n);
+}
+
 void launch_extrap_stage(const RowArgs& a0, cudaStream_t st) {
   RowArgs a = a0;
   set_vec8(a);
   const long long items = ((a.nx % 64) == 0 && a.vec8) ? (long long)a.rows * (a.nx / 2) : a.N;
   extrap_stage_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(a);
 }
-bool prepare_row(int Lx, int prec) { return row_dispatch(Lx, -1, prec, nullptr, nullptr, nullptr); }
+bool prepare_row(int Lx, int prec) {
+  if (mixed_len(Lx)) return prec <= 0 && row_dispatch_mixed(Lx, -1, nullptr, nullptr, nullptr);
+  if (prec <= 0) pipe_dispatch(Lx, -1, nullptr, nullptr, nullptr);
+  return row_dispatch(Lx, -1, prec, nullptr, nullptr, nullptr);
+}
 
 }  // namespace gbd

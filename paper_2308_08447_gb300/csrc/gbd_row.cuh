@@ -173,13 +173,14 @@ __device__ __forceinline__ bool epilogue_pair(const RowArgs& a, int mode, int z,
       *reinterpret_cast<float2*>(a.kout + c * N + idx) = make_float2(res[0][c], res[1][c]);
       if (!a.mnext) continue;
       float2 s = *reinterpret_cast<const float2*>(a.m0 + c * N + idx);
+      const float hs = a.hdev ? *a.hdev : 1.f;   // step size on the device, or folded into kw
       for (int j = 0; j < a.nk; ++j) {
         const float2 kj = *reinterpret_cast<const float2*>(a.kin[j] + c * N + idx);
-        s.x = fmaf(a.kw[j], kj.x, s.x);
-        s.y = fmaf(a.kw[j], kj.y, s.y);
+        s.x = fmaf(a.kw[j] * hs, kj.x, s.x);
+        s.y = fmaf(a.kw[j] * hs, kj.y, s.y);
       }
-      s.x = fmaf(a.kw[a.nk], res[0][c], s.x);
-      s.y = fmaf(a.kw[a.nk], res[1][c], s.y);
+      s.x = fmaf(a.kw[a.nk] * hs, res[0][c], s.x);
+      s.y = fmaf(a.kw[a.nk] * hs, res[1][c], s.y);
       *reinterpret_cast<float2*>(a.mnext + c * N + idx) = s;
       mn[0][c] = s.x;
       mn[1][c] = s.y;
@@ -249,8 +250,10 @@ __device__ __forceinline__ bool epilogue_cell(const RowArgs& a, int mode, int z,
     const float* __restrict__ p = a.ms + c * N;
     const float mc = p[idx];
     mv[c] = mc;
-    lap[c] = a.cx * (p[ixp] - 2.f * mc + p[ixm]) + a.cy * (p[iyp] - 2.f * mc + p[iym]) +
-             a.cz * (p[izp] - 2.f * mc + p[izm]);
+    // (minus - 2 centre + plus) per axis, the operand order of epilogue_pair, so that every
+    // epilogue path rounds alike
+    lap[c] = a.cx * (p[ixm] - 2.f * mc + p[ixp]) + a.cy * (p[iym] - 2.f * mc + p[iyp]) +
+             a.cz * (p[izm] - 2.f * mc + p[izp]);
   }
   float m0v[3] = {}, accv[3] = {};
   if (mode == ROW_RKG) {
@@ -261,8 +264,9 @@ __device__ __forceinline__ bool epilogue_cell(const RowArgs& a, int mode, int z,
       a.kout[c * N + idx] = res[c];
       if (!a.mnext) continue;
       float s = a.m0[c * N + idx];
-      for (int j = 0; j < a.nk; ++j) s = fmaf(a.kw[j], a.kin[j][c * N + idx], s);
-      s = fmaf(a.kw[a.nk], res[c], s);
+      const float hs = a.hdev ? *a.hdev : 1.f;
+      for (int j = 0; j < a.nk; ++j) s = fmaf(a.kw[j] * hs, a.kin[j][c * N + idx], s);
+      s = fmaf(a.kw[a.nk] * hs, res[c], s);
       a.mnext[c * N + idx] = s;
       mn[c] = s;
     }

@@ -165,35 +165,48 @@ void tensor_at(int X, int Y, int Z, double dx, double dy, double dz, double out[
     dipole_quadrature(px, py, pz, dx, dy, dz, r < 16.0 ? 4 : (r < 64.0 ? 3 : 2), out);
 }
 
-// ---- FP64 host FFT (radix-2, in place) -------------------------------------------------------
+// ---- FP64 host FFT (mixed radix, any length) -------------------------------------------------
+// Decimation in time: a length-n transform (n = p m, p the smallest prime factor of n) is p
+// length-m transforms of the samples t, t + p, t + 2p, ... followed by
+//   X[q + s m] = sum_t W_n^(t (q + s m)) Y_t[q],  W_n = exp(-2 pi i / n),
+// recursively; W_n^j comes from the table of the whole length N at index j N / n. The padded
+// lengths here are 2^a 3^b 5^c, so every stage is a short sum.
 struct Fft1 {
-  int n = 0, logn = 0;
-  std::vector<std::complex<double>> w;
-  std::vector<int> rev;
-  explicit Fft1(int n_) : n(n_) {
-    while ((1 << logn) < n) ++logn;
-    w.resize(n / 2 > 0 ? n / 2 : 1);
-    for (int k = 0; k < n / 2; ++k) w[k] = std::polar(1.0, -2.0 * PI * k / n);
-    rev.resize(n);
-    for (int i = 0; i < n; ++i) {
-      int r = 0;
-      for (int b = 0; b < logn; ++b)
-        if (i & (1 << b)) r |= 1 << (logn - 1 - b);
-      rev[i] = r;
+  int n = 0;
+  std::vector<std::complex<double>> w;      // exp(-2 pi i k / n), k < n
+  explicit Fft1(int n_) : n(n_), w(n_ > 0 ? n_ : 1) {
+    for (int k = 0; k < n; ++k) w[k] = std::polar(1.0, -2.0 * PI * k / n);
+  }
+  static int smallest_factor(int m) {
+    for (int f = 2; f * f <= m; ++f)
+      if (m % f == 0) return f;
+    return m;
+  }
+  // out[0 .. len) = DFT of in[0], in[stride], ..., in[(len - 1) stride]; out and in do not overlap
+  void rec(const std::complex<double>* in, std::complex<double>* out, int len, int stride) const {
+    if (len == 1) {
+      out[0] = in[0];
+      return;
+    }
+    const int p = smallest_factor(len), m = len / p;
+    for (int t = 0; t < p; ++t) rec(in + t * stride, out + t * m, m, stride * p);
+    const int step = n / len;   // W_len^j = w[j step]
+    std::complex<double> y[8];
+    for (int q = 0; q < m; ++q) {
+      for (int t = 0; t < p; ++t) y[t] = out[t * m + q];
+      for (int s = 0; s < p; ++s) {
+        std::complex<double> acc = 0.0;
+        for (int t = 0; t < p; ++t) acc += y[t] * w[((long long)t * (q + s * m) % len) * step];
+        out[s * m + q] = acc;
+      }
     }
   }
+  // in place; shared by the threads of a parallel loop (each has its own copy buffer)
   void forward(std::complex<double>* a) const {
-    for (int i = 0; i < n; ++i)
-      if (i < rev[i]) std::swap(a[i], a[rev[i]]);
-    for (int len = 2; len <= n; len <<= 1) {
-      const int step = n / len;
-      for (int i = 0; i < n; i += len)
-        for (int j = 0; j < len / 2; ++j) {
-          std::complex<double> u = a[i + j], v = a[i + j + len / 2] * w[j * step];
-          a[i + j] = u + v;
-          a[i + j + len / 2] = u - v;
-        }
-    }
+    if (n <= 1) return;
+    thread_local std::vector<std::complex<double>> tmp;
+    tmp.assign(a, a + n);
+    rec(tmp.data(), a, n, 1);
   }
 };
 

@@ -64,6 +64,7 @@ _SIG = {
                                              ctypes.c_size_t],
     "gbd_demag_noalloc": [_P, _P, _P, _P],
     "gbd_mesh_autotune": [_P, _P],
+    "gbd_mesh_plan_dims": [_P, ctypes.POINTER(_I)],
     "gbd_mesh_get_tuning": [_P, ctypes.POINTER(_I)],
     "gbd_mesh_set_tuning": [_P, ctypes.POINTER(_I)],
     "gbd_batch_create": [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)],
@@ -108,11 +109,11 @@ def _check(status):
         raise GbdError(status, load().gbd_last_error().decode())
 
 
-GBD_FLAG_PBC_X, GBD_FLAG_PBC_Y, GBD_FLAG_PBC_Z = 1, 2, 4
+GBD_FLAG_PBC_X, GBD_FLAG_PBC_Y, GBD_FLAG_PBC_Z, GBD_FLAG_POW2_PAD = 1, 2, 4, 8
 
 
 def make_desc(n, cell, Ms, A_ex=0.0, alpha=0.0, gamma=0.0, Hext=(0.0, 0.0, 0.0), precision=GBD_FP32, pbc=(False,) * 3,
-              pbc_images=0):
+              pbc_images=0, pow2_pad=False):
     d = gbd_mesh_desc()
     d.nx, d.ny, d.nz = (int(v) for v in n)
     d.dx, d.dy, d.dz = (float(v) for v in cell)
@@ -120,6 +121,8 @@ def make_desc(n, cell, Ms, A_ex=0.0, alpha=0.0, gamma=0.0, Hext=(0.0, 0.0, 0.0),
     d.Hext[0], d.Hext[1], d.Hext[2] = (float(v) for v in Hext)
     d.precision = int(precision)
     d.flags = (GBD_FLAG_PBC_X if pbc[0] else 0) | (GBD_FLAG_PBC_Y if pbc[1] else 0) | (GBD_FLAG_PBC_Z if pbc[2] else 0)
+    if pow2_pad:
+        d.flags |= GBD_FLAG_POW2_PAD
     d.pbc_images = int(pbc_images)
     return d
 
@@ -324,6 +327,13 @@ def gbd_plan_dims(desc):
     return tuple(out)
 
 
+def gbd_mesh_plan_dims(mesh):
+    """(Px, Py, Pz, Hx, Ky, Kz) of the plan the mesh uses now (the autotuner may change it)."""
+    out = (ctypes.c_int * 6)()
+    _check(load().gbd_mesh_plan_dims(mesh, out))
+    return tuple(out)
+
+
 def gbd_kernel_spectrum_host(desc):
     import numpy as np
     Px, Py, Pz, Hx, Ky, Kz = gbd_plan_dims(desc)
@@ -349,11 +359,11 @@ class Mesh:
     """One mesh: owns the library handle; the kernel spectrum is computed on construction."""
 
     def __init__(self, n, cell, Ms, A_ex=0.0, alpha=0.0, gamma=0.0, Hext=(0.0, 0.0, 0.0),
-                 precision=GBD_FP32, set_kernel=True, stream=None, pbc=(False,) * 3, pbc_images=0):
+                 precision=GBD_FP32, set_kernel=True, stream=None, pbc=(False,) * 3, pbc_images=0, pow2_pad=False):
         self.n = tuple(int(v) for v in n)
         self.pbc = tuple(bool(v) for v in pbc)
         self.shape = (3, self.n[2], self.n[1], self.n[0])
-        self.desc = make_desc(n, cell, Ms, A_ex, alpha, gamma, Hext, precision, pbc, pbc_images)
+        self.desc = make_desc(n, cell, Ms, A_ex, alpha, gamma, Hext, precision, pbc, pbc_images, pow2_pad)
         self.handle = gbd_mesh_create(self.desc)
         if set_kernel:
             gbd_set_kernel(self.handle, stream)

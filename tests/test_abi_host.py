@@ -36,9 +36,25 @@ def test_library_exports_every_header_symbol(g):
                                     ((32, 32, 8), (64, 64, 16, 33, 33, 9)),
                                     ((512, 512, 64), (1024, 1024, 128, 513, 513, 65)),
                                     ((1, 1, 1), (2, 1, 1, 2, 1, 1)),
-                                    ((33, 17, 5), (128, 64, 16, 65, 33, 9))])
+                                    ((33, 17, 5), (128, 64, 16, 65, 33, 9)),
+                                    # lengths 3 * 2^k, 5 * 2^k where shorter than the power of two
+                                    ((352, 480, 1), (768, 1024, 1, 385, 513, 1)),
+                                    ((96, 96, 1), (192, 192, 1, 97, 97, 1)),
+                                    ((160, 64, 4), (320, 128, 8, 161, 65, 5)),
+                                    ((640, 320, 2), (1280, 640, 4, 641, 321, 3)),
+                                    ((300, 150, 1), (640, 320, 1, 321, 161, 1))])
 def test_plan_dims(g, n, dims):
     assert g.gbd_plan_dims(g.make_desc(n, (1e-9, 1e-9, 1e-9), 8e5)) == dims
+
+
+@pytest.mark.parametrize("n", [(352, 480, 1), (160, 64, 4), (300, 150, 1)])
+def test_plan_dims_powers_of_two_when_asked(g, n):
+    # GBD_FLAG_POW2_PAD, and the split precisions, keep every padded length a power of two
+    for d in (g.make_desc(n, (1e-9,) * 3, 8e5, pow2_pad=True),
+              g.make_desc(n, (1e-9,) * 3, 8e5, precision=g.GBD_SPLIT_BF16)):
+        Px, Py, Pz = g.gbd_plan_dims(d)[:3]
+        for P, m in ((Px, n[0]), (Py, n[1]), (Pz, n[2])):
+            assert P & (P - 1) == 0 and P >= 2 * m - 1
 
 
 def test_argument_errors(g):
@@ -65,7 +81,9 @@ def test_mesh_bytes_counts_buffers(g):
     S = 3 * 1025 * 1024 * 8
     K = 1025 * 1025 * 16
     state = 9 * N * 4
-    twiddles = 2 * 8192 * 8 + 4 * 32 * 32 * 4   # power-of-two levels up to 8192; split DFT-16 fragments
+    # power-of-two levels up to 8192; split DFT-16 fragments; levels 3 * 2^j (up to 6144) and
+    # 5 * 2^j (up to 5120)
+    twiddles = 2 * 8192 * 8 + 4 * 32 * 32 * 4 + 2 * 6144 * 8 + 2 * 5120 * 8
     assert b == S + K + state + twiddles
 
 
@@ -103,7 +121,9 @@ def test_library_tensor_matches_exact_golden(g):
 
 @pytest.mark.parametrize("n,cell", [((8, 6, 1), (2e-9, 2e-9, 3e-9)), ((5, 4, 3), (2e-9, 3e-9, 4e-9)),
                                     ((1, 1, 1), (3e-9, 3e-9, 3e-9)), ((1, 7, 4), (1e-9, 1e-9, 2e-9)),
-                                    ((16, 1, 1), (1e-9, 1e-9, 1e-9)), ((32, 32, 8), (4e-9, 4e-9, 4e-9))])
+                                    ((16, 1, 1), (1e-9, 1e-9, 1e-9)), ((32, 32, 8), (4e-9, 4e-9, 4e-9)),
+                                    ((80, 48, 2), (2e-9, 2e-9, 3e-9)),    # Px = 192, Py = 96
+                                    ((150, 72, 1), (3e-9, 3e-9, 3e-9))])  # Px = 320, Py = 160
 def test_library_spectrum_matches_oracle_fft(g, n, cell):
     desc = g.make_desc(n, cell, 8e5)
     Px, Py, Pz, Hx, Ky, Kz = g.gbd_plan_dims(desc)

@@ -4,7 +4,8 @@ of a failed mesh creation.
 Every caller field sits inside a larger allocation between two guard regions filled with a
 sentinel bit pattern; after each public call the guards must be bit-identical. The cases cover
 the scalar path (odd sizes, fields 4-byte aligned), the vector path (nx a multiple of 64, 8-byte
-aligned), a 3D mesh, a periodic mesh, and every compute call that writes a caller field.
+aligned), a 3D mesh, a periodic mesh, and every compute call that writes a caller field
+(gbd_demag_noalloc included).
 """
 import os
 
@@ -59,6 +60,8 @@ def test_guard_words_untouched(g, n, cell, pbc, shift):
     M = Guarded(shape, 8e5 * m0, shift)
     H = Guarded(shape, np.zeros(shape), shift)
     mesh.demag(M.t, H.t)
+    assert M.guards_intact() and H.guards_intact()
+    g.gbd_demag_noalloc(mesh.handle, M.t, H.t, shape)   # the same field through the static scratch
     assert M.guards_intact() and H.guards_intact()
     m = Guarded(shape, m0, shift)
     mesh.effective_field(m.t, H.t)

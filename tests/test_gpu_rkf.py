@@ -120,3 +120,32 @@ def test_extrapolated_adaptive_run_close_to_fine_reference(g):
     # stage fields), so the run sits further from the reference than the exact one (1.2e-4
     # measured against <= 1e-4)
     assert acc >= 6 and np.abs(got - ref).max() < 3e-4
+
+
+def test_device_controlled_run_matches_host_loop(g):
+    # Without extrapolation gbd_llg_run_rkf56 runs as one CUDA graph whose loop node repeats
+    # attempt -> step control -> accept on the device; with per-launch timing on, the same run
+    # takes the host loop (one stream wait per attempt). Both follow the same rule, so they take
+    # the same steps; the weights h a_ij are formed in FP32 on the device instead of FP64 on the
+    # host, so the states agree to rounding.
+    n, cell, Ms, A, alpha = (64, 48, 2), (3e-9, 3e-9, 3e-9), 8e5, 1.3e-11, 0.1
+    m = W.random_unit(n, 84)
+    mesh = g.Mesh(n, cell, Ms, A_ex=A, alpha=alpha, Hext=(0.0, 0.0, 3e4))
+    dev, host = to_dev(m), to_dev(m)
+    nd, ad, rd = mesh.run_rkf56(dev, 2e-12, 1e-14, 1e-5)
+    g.gbd_mesh_set_timing(mesh.handle, True)
+    nh, ah, rh = mesh.run_rkf56(host, 2e-12, 1e-14, 1e-5)
+    g.gbd_mesh_read_timing(mesh.handle)
+    g.gbd_mesh_set_timing(mesh.handle, False)
+    assert (ad, rd) == (ah, rh) and ad > 3
+    assert nd == pytest.approx(nh, rel=1e-4)
+    assert np.abs(to_host(dev) - to_host(host)).max() < 1e-5
+    # the attempt limit ends the device loop
+    m3 = to_dev(m)
+    _, a3, r3 = mesh.run_rkf56(m3, 1e-9, 1e-15, 1e-5, max_steps=3)
+    assert a3 + r3 == 3
+    # t_end = 0: nothing runs, dt comes back unchanged
+    m0 = to_dev(m)
+    nz_, a0, r0 = mesh.run_rkf56(m0, 0.0, 2e-14, 1e-5)
+    assert (a0, r0) == (0, 0) and nz_ == 2e-14 and np.array_equal(to_host(m0), m.astype(np.float64))
+    mesh.close()

@@ -72,6 +72,13 @@ def test_malformed_state_refused(g):
     with pytest.raises(g.GbdError) as ei:          # another cell count
         other.set_state(state)
     assert ei.value.status == g.GBD_EINVAL
+    # the same cell count in another shape (transposed, or split over z) has another slot layout
+    for shape in ((16, 64, 1), (32, 16, 2)):
+        same_n = g.Mesh(shape, (2e-9, 2e-9, 3e-9), 8e5, A_ex=1.3e-11, alpha=0.1)
+        with pytest.raises(g.GbdError) as ei:
+            same_n.set_state(state)
+        assert ei.value.status == g.GBD_EINVAL
+        same_n.close()
     mesh.set_state(state)                            # the intact image still loads
     other.close()
     mesh.close()

@@ -69,3 +69,30 @@ def test_batch_recaptures_after_set_params(g):
     batch.close()
     mesh.close()
     ref.close()
+
+
+def test_time_step_study_against_fp64_reference(g):
+    """The time-step study of Fig. 2 against double precision: the reduced switching film from the
+    FP64 oracle's S state, 1 ns at 100 fs on the FP32 GPU path, <m> every 10 ps, against the
+    oracle's FP64 RK4 trajectory at 50 fs (tests/golden, make_switching_reference.py). The paper
+    reports an FP32 floor of eps ~ 1e-4 at every time step (Sec. II); the bound here is ten times
+    that, and the run must track the reference far better than the trajectory moves."""
+    import os
+    import torch
+    from oracle import llg as L
+    gold = os.path.join(os.path.dirname(__file__), "golden")
+    m_s = np.load(os.path.join(gold, "switching_96x48x2_S_state.npy"))
+    ref = np.loadtxt(os.path.join(gold, "switching_96x48x2_fp64_traj.txt"))
+    spec = W.switching(scale=5)
+    mesh = g.Mesh(spec.n, spec.cell, spec.Ms, A_ex=spec.A_ex, alpha=spec.alpha, Hext=spec.Hext)
+    m = to_dev(m_s)
+    rec = []
+    for _ in range(len(ref)):
+        mesh.llg_step(m, 100, 100e-15)
+        rec.append(m.double().mean(dim=(1, 2, 3)))
+    traj = torch.stack(rec).cpu().numpy()
+    mesh.close()
+    eps = L.trajectory_error(traj, ref, 1.0)
+    assert eps <= 1e-3, eps
+    # the switching field moves <m> by far more than that over the nanosecond
+    assert L.trajectory_error(ref, np.broadcast_to(ref[0], ref.shape), 1.0) > 0.1

@@ -6,7 +6,8 @@ memory cap where an allocation (and the device synchronisation it may bring) is 
 acceptable. For them the library keeps the demag scratch (the x spectrum, and the y spectrum
 of 3D meshes) in a fixed device array compiled into the library. These tests call that entry
 point through the C ABI and check that it returns what gbd_demag returns, on two calls in a
-row with different inputs, and that a mesh too large for the array is refused up front.
+row with different inputs, that on the 1024 x 1024 film it also meets the FP32 tolerance against
+the FP64 oracle on its own, and that a mesh too large for the array is refused up front.
 
 This file is named so that pytest collects it last.
 """
@@ -14,6 +15,8 @@ import numpy as np
 import pytest
 
 from gpu_util import TOL_FP32, e_inf, lib, to_dev, to_host
+from oracle import conv as C
+from oracle import tensor as T
 from paper_2308_08447_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -52,3 +55,15 @@ def test_noalloc_refuses_mesh_beyond_static_scratch(g):
     assert ei.value.status == g.GBD_EBUDGET
     assert "static maximum" in g.gbd_last_error()
     mesh.close()
+
+
+def test_noalloc_film_against_oracle(g):
+    spec = W.thin_film()
+    M = (spec.Ms * W.vortex_noise(spec.n, spec.cell, spec.seed)).astype(np.float32)
+    mesh = g.Mesh(spec.n, spec.cell, spec.Ms)
+    H = to_dev(np.full_like(M, np.nan))
+    g.gbd_demag_noalloc(mesh.handle, to_dev(M), H, mesh.shape)
+    got = to_host(H)
+    mesh.close()
+    Href = C.fft_conv(M.astype(np.float64), T.tensor_all_offsets(spec.n, spec.cell))
+    assert e_inf(got, Href) <= TOL_FP32
