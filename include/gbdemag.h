@@ -248,17 +248,19 @@ const char* gbd_last_error(void);
 
 /* ---- tile-shape autotuning ---------------------------------------------------------------
  * Every kernel family has two tile shapes (lines of the transform per thread block); the x-row
- * pass has a third variant, 2 (FP32 meshes): a persistent kernel, one block per SM, that copies
- * the next row group's spectrum tile and field rows into shared memory (cp.async) while it
- * transforms the current group, used where it applies (x transform length Px/2 in [64, 2048],
- * open x axis, nx a multiple of 4, ny a multiple of the group's rows, the staged fields
- * 16-byte aligned; otherwise variant 1 runs). A new mesh starts with variant 1 everywhere. All variants give identical
+ * pass has two more variants for FP32 meshes, 2 and 3: a persistent kernel that copies the next
+ * row group's inputs into shared memory (cp.async) while it transforms the current group -- in
+ * RK stages variant 2 stages the spectrum tile and the field rows (one block per SM), variant 3
+ * the spectrum tile only (two blocks per SM; nx a multiple of 64); transform-only launches stage
+ * their input (two blocks per SM). They are used where they apply (x transform length Px/2 in
+ * [64, 2048], open x axis, nx a multiple of 4, ny a multiple of the group's rows, the staged
+ * fields 16-byte aligned; otherwise variant 1 runs). A new mesh starts with variant 1. All variants give identical
  * results -- each line's FFT and each cell's update do not depend on how lines are grouped --
  * and differ only in speed, which depends on the mesh size. gbd_mesh_autotune times the
  * variants of each pass this mesh uses (on its own buffers, which it zeroes; the stream is
  * synchronized) and keeps the fastest; results are cached per (nx, ny, nz, device) in the
  * process and, when the environment variable GBD_AUTOTUNE_CACHE names a file, in that text
- * file. Requires gbd_set_kernel. Variants (row, film, y, z): row 0, 1 or 2, the others 0 or 1.
+ * file. Requires gbd_set_kernel. Variants (row, film, y, z): row 0 to 3, the others 0 or 1.
  * The autotuner also chooses the padded lengths: a mesh planned with a 3 * 2^k or 5 * 2^k
  * length (see GBD_FLAG_POW2_PAD) is timed against the same mesh on power-of-two lengths (a
  * scratch twin with its own tuned tiles), and moves onto the power-of-two plan when that is

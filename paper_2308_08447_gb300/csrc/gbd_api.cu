@@ -1465,8 +1465,8 @@ void read_tune_file_locked() {
   std::array<int, 6> v;
   while (std::fscanf(f, "%d %d %d %d %d %d %d %d %d %d %d %d %d", &k.nx, &k.ny, &k.nz, &k.dev, &k.Px, &k.Py, &k.prec,
                      &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]) == 13) {
-    bool ok = (v[4] == 0 || v[4] == 1) && v[5] >= 0 && v[5] <= 2;
-    for (int i = 0; i < 4; ++i) ok = ok && (v[i] == 0 || v[i] == 1 || (i == 0 && v[i] == 2));
+    bool ok = (v[4] == 0 || v[4] == 1) && v[5] >= 0 && v[5] <= 3;
+    for (int i = 0; i < 4; ++i) ok = ok && (v[i] == 0 || v[i] == 1 || (i == 0 && (v[i] == 2 || v[i] == 3)));
     if (ok) g_tune[k] = v;
   }
   std::fclose(f);
@@ -1622,8 +1622,8 @@ extern "C" gbd_status gbd_mesh_set_tuning(gbd_mesh* m, const int in[4]) {
   if (!m || !in) return fail(GBD_EINVAL, "NULL argument");
   std::array<int, 4> v;
   for (int i = 0; i < 4; ++i) {
-    if (in[i] != 0 && in[i] != 1 && !(i == 0 && in[i] == 2))
-      return fail(GBD_EINVAL, "tile variants are 0 or 1 (row: 0, 1 or 2)");
+    if (in[i] != 0 && in[i] != 1 && !(i == 0 && (in[i] == 2 || in[i] == 3)))
+      return fail(GBD_EINVAL, "tile variants are 0 or 1 (row: 0 to 3)");
     v[i] = in[i];
   }
   apply_tuning(m, v);
@@ -1659,7 +1659,7 @@ extern "C" gbd_status gbd_mesh_autotune(gbd_mesh* m, void* stream) {
   const int reps = 5;
   std::array<int, 4> best = {p.var_row, p.var_film, p.var_y, p.var_z};
   auto pick = [&](int slot, auto launch_v, int nvar = 2) -> cudaError_t {
-    float t[3];
+    float t[4];
     for (int v = 0; v < nvar; ++v) {
       cudaError_t ee = time_variant(st, reps, [&] { launch_v(v); }, &t[v]);
       if (ee != cudaSuccess) return ee;
@@ -1681,7 +1681,7 @@ extern "C" gbd_status gbd_mesh_autotune(gbd_mesh* m, void* stream) {
   ra.acc = m->acc;
   ra.mode = gbd::ROW_RK2;
   ra.fwd_after = 1;
-  e = pick(0, [&](int v) { gbd::launch_row(p.Lx, v, p.prec, ra, m->tw, st); }, p.prec == 0 ? 3 : 2);
+  e = pick(0, [&](int v) { gbd::launch_row(p.Lx, v, p.prec, ra, m->tw, st); }, p.prec == 0 ? 4 : 2);
   // the transform-only x-row launches: a forward transform and an inverse one to H_d
   int best_io = p.var_row_io;
   if (e == cudaSuccess) {

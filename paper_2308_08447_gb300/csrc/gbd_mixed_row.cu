@@ -39,8 +39,8 @@ bool row_dispatch_mixed(int Lx, int var, const RowArgs* a, const float2* tw, cud
       row_launch_t<LX, row_rb(LX, 0), 0>(nullptr, nullptr, nullptr);
     });
   }
-  if (var == 2) {
-    const int kind = pipe_kind(Lx, *a);
+  if (var >= 2) {
+    const int kind = pipe_kind(Lx, *a, var);
     if (kind >= 0 && pipe_dispatch_with(sw, Lx, kind, a, tw, st)) return true;
   }
   return mixed_switch(Lx, [&](auto lx) {

@@ -121,17 +121,18 @@ static void set_vec8(RowArgs& a) {
   a.vec8 = ok ? 1 : 0;
 }
 
-// Tile variant 2 is the persistent pipelined kernel (gbd_rowpipe.cuh, FP32 only) where it
-// applies; other launches of variant 2 take row_kernel's variant 1.
+// Tile variants 2 and 3 are the persistent pipelined kernel (gbd_rowpipe.cuh, FP32 only) where it
+// applies (3: the RK stages stage only the spectrum tile, two blocks per SM); other launches of
+// variants 2 and 3 take row_kernel's variant 1.
 bool launch_row(int Lx, int var, int prec, const RowArgs& a0, const float2* tw, cudaStream_t st) {
   RowArgs a = a0;
   set_vec8(a);
   if (mixed_len(Lx)) return prec == 0 && row_dispatch_mixed(Lx, var, &a, tw, st);
-  if (var == 2 && prec == 0) {
-    const int kind = pipe_kind(Lx, a);
+  if (var >= 2 && prec == 0) {
+    const int kind = pipe_kind(Lx, a, var);
     if (kind >= 0) return pipe_dispatch(Lx, kind, &a, tw, st);
   }
-  return row_dispatch(Lx, var == 2 ? 1 : var, prec, &a, tw, st);
+  return row_dispatch(Lx, var >= 2 ? 1 : var, prec, &a, tw, st);
 }
 
 // One warp: lane l writes register r of each table at word r * 32 + l (Dft16Frags::load).

@@ -23,7 +23,10 @@
 
 namespace gbd {
 
-enum PipeKind : int { PIPE_FWD = 0, PIPE_INV = 1, PIPE_RK = 2 };
+// PIPE_RK stages the spectrum tile and the epilogue's field rows (one block per SM); PIPE_RKS
+// stages only the spectrum tile and reads the field rows in the epilogue (epilogue_pair), which
+// leaves room for two blocks per SM.
+enum PipeKind : int { PIPE_FWD = 0, PIPE_INV = 1, PIPE_RK = 2, PIPE_RKS = 3 };
 
 // rows per group: 2048 complex values per component (LX in [64, 2048]); for LX = 3 * 2^k or
 // 5 * 2^k, 2048 over the next power of two above LX
@@ -65,6 +68,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // blocks per SM: the RK stage stages its field rows and fills the SM alone; the forward-only and
 // inverse-only launches stage half as much and run two blocks per SM
 __host__ __device__ constexpr int pipe_blocks(int K) { return K == PIPE_RK ? 1 : 2; }
+__host__ __device__ constexpr bool pipe_rk(int K) { return K == PIPE_RK || K == PIPE_RKS; }
 
 template <int LX, int K>
 __global__ void __launch_bounds__(3 * pipe_rb(LX) * LX / GBD_E, pipe_blocks(K))
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(3 * pipe_rb(LX) * LX / GBD_E, pipe_blocks(K))
 
   int g = blockIdx.x;
   if constexpr (K != PIPE_FWD) issue_spectrum(g);
-  if constexpr (K != PIPE_INV) issue_fields(g);
+  if constexpr (K == PIPE_RK || K == PIPE_FWD) issue_fields(g);
   for (; g < ngroups; g += gridDim.x) {
     const int gn = g + gridDim.x;
     const int row0 = g * RB;
@@ -220,7 +224,27 @@ __global__ void __launch_bounds__(3 * pipe_rb(LX) * LX / GBD_E, pipe_blocks(K))
       continue;   // the next iteration's barrier orders these reads before the lines are rewritten
     }
 
-    if constexpr (K == PIPE_RK) {
+    if constexpr (K == PIPE_RKS) {
+      // 3. exchange + LLG + RK stage per pair of cells, the field rows read from global memory:
+      //    the 32 lanes of a warp take 32 consecutive pairs of one row (nx a multiple of 64)
+      const int NP2 = nx / 2;
+      for (int e = threadIdx.x; e < RB * NP2; e += T) {
+        const int rr = e / NP2;
+        const int xp = e - rr * NP2;
+        const long long idx = (long long)(row0 + rr) * nx + 2 * xp;
+        float hd[2][3], mn[2][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float2 h2 = lines[(c * RB + rr) * LS + pad(xp)];
+          hd[0][c] = h2.x * a.hscale;
+          hd[1][c] = h2.y * a.hscale;
+        }
+        if (epilogue_pair(a, mode, z, y0 + rr, idx, 2 * xp, threadIdx.x & 31, hd, mn) && a.fwd_after) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) lines[(c * RB + rr) * LS + pad(xp)] = make_float2(mn[0][c], mn[1][c]);
+        }
+      }
+    } else if constexpr (K == PIPE_RK) {
       // 3. exchange + LLG + RK stage per pair of cells, from the staged rows
       const int NP2 = nx / 2;
       const long long sz = (long long)nx * ny;
@@ -298,7 +322,7 @@ __global__ void __launch_bounds__(3 * pipe_rb(LX) * LX / GBD_E, pipe_blocks(K))
       }
     }
     // cells nx .. LX-1 of each line are zero padding for the forward transform
-    if (nx < LX && (K != PIPE_RK || a.fwd_after)) {
+    if (nx < LX && (!pipe_rk(K) || a.fwd_after)) {
       for (int e = threadIdx.x; e < LINES * (LX - nx); e += T) {
         const int line = e / (LX - nx);
         const int x = nx + e % (LX - nx);
@@ -306,8 +330,8 @@ __global__ void __launch_bounds__(3 * pipe_rb(LX) * LX / GBD_E, pipe_blocks(K))
       }
     }
     __syncthreads();
-    issue_fields(gn);       // the staged rows have been consumed
-    if (K == PIPE_RK && !a.fwd_after) continue;   // uniform over the grid
+    if constexpr (K == PIPE_RK || K == PIPE_FWD) issue_fields(gn);   // the staged rows have been consumed
+    if (pipe_rk(K) && !a.fwd_after) continue;   // uniform over the grid
     // 4. forward FFT; the first pass reads the lower half only (the upper half is zero)
     {
       auto ld_half = [&](int line, int i) { return i < HALF ? lines[line * LS + pad(i)] : make_float2(0.f, 0.f); };
@@ -316,12 +340,14 @@ __global__ void __launch_bounds__(3 * pipe_rb(LX) * LX / GBD_E, pipe_blocks(K))
       __syncthreads();
       fwd_passes_smem<-1, LX, false, LINES, false, LS, 1, NP, 0>(lines, tw);
     }
-    // 5. Z -> X pairwise and store the half spectrum, VR adjacent rows per vector
+    // 5. Z -> X pairwise and store the half spectrum, VR adjacent rows per vector; adjacent lanes
+    //    take the row groups of one frequency, so that a lane pair writes whole 32-byte sectors
+    //    of the [kx][y] spectrum (RB = 4)
     for (int e = threadIdx.x; e < RG * 3 * (HALF + 1); e += T) {
-      const int k = e % (HALF + 1);
-      const int t2 = e / (HALF + 1);
-      const int c = t2 % 3;
-      const int gg = t2 / 3;
+      const int gg = e % RG;
+      const int t2 = e / RG;
+      const int k = t2 % (HALF + 1);
+      const int c = t2 / (HALF + 1);
       const float2 wp = twiddle_at<-1>(tw, 2 * LX, k);
       const float2 wm = cconj(wp);
       float2 xk[VR], xl[VR];
@@ -372,16 +398,18 @@ static void pipe_launch_t(const RowArgs* a, const float2* tw, cudaStream_t st) {
   row_pipe_kernel<LX, K><<<grid, T, smem, st>>>(*a, tw, ngroups);
 }
 
-// The kind of pipelined launch that serves a (-1: none; the caller uses row_kernel). a.vec8 must
-// be set. The staged rows are copied in 16-byte pieces, so the fields read through the staging
-// buffers must be 16-byte aligned and nx a multiple of 4; a group's RB rows lie in one plane.
-static int pipe_kind(int Lx, const RowArgs& a) {
+// The kind of pipelined launch that serves a for tile variant var (2: RK stages stage their field
+// rows, 3: they read them directly) (-1: none; the caller uses row_kernel). a.vec8 must be set.
+// The staged rows are copied in 16-byte pieces, so the fields read through the staging buffers
+// must be 16-byte aligned and nx a multiple of 4; a group's RB rows lie in one plane.
+static int pipe_kind(int Lx, const RowArgs& a, int var) {
   auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
   if (Lx < 64 || Lx > 2048 || (a.per & 1) || a.extrap || !a.vec8 || a.nx % 4 != 0 || a.ny % pipe_rb(Lx) != 0)
     return -1;
   if (a.mode == ROW_FWD) return al16(a.in) ? PIPE_FWD : -1;
   if (a.mode == ROW_H) return (a.hrec == nullptr) ? PIPE_INV : -1;
   if (a.mode >= ROW_RK1 && a.mode <= ROW_RK4) {
+    if (var == 3) return (a.nx % 64 == 0) ? PIPE_RKS : -1;
     const bool reads_acc = a.mode != ROW_RK1;
     return (al16(a.ms) && (!reads_acc || (al16(a.m0) && al16(a.acc)))) ? PIPE_RK : -1;
   }
@@ -399,6 +427,7 @@ static bool pipe_dispatch_with(SW sw, int Lx, int kind, const RowArgs* a, const 
       if (kind < 0 || kind == PIPE_FWD) pipe_launch_t<LX, PIPE_FWD>(a, tw, st);
       if (kind < 0 || kind == PIPE_INV) pipe_launch_t<LX, PIPE_INV>(a, tw, st);
       if (kind < 0 || kind == PIPE_RK) pipe_launch_t<LX, PIPE_RK>(a, tw, st);
+      if (kind < 0 || kind == PIPE_RKS) pipe_launch_t<LX, PIPE_RKS>(a, tw, st);
     }
   };
   if (Lx < 64 || Lx > 2048) return false;

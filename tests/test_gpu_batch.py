@@ -40,7 +40,8 @@ def test_tile_variants_bit_identical(g, n, cell, Ms):
     mesh = _mesh(g, n, cell, Ms)
     m = W.random_unit(n, 41)
     outs = []
-    for v in ((0, 0, 0, 0), (1, 1, 1, 1), (2, 0, 1, 0)):   # row variant 2: the pipelined kernel
+    # row variants 2 and 3: the pipelined kernel (field rows staged, or read directly)
+    for v in ((0, 0, 0, 0), (1, 1, 1, 1), (2, 0, 1, 0), (3, 1, 0, 1)):
         g.gbd_mesh_set_tuning(mesh.handle, v)
         assert g.gbd_mesh_get_tuning(mesh.handle) == v
         md = to_dev(m)
@@ -51,7 +52,7 @@ def test_tile_variants_bit_identical(g, n, cell, Ms):
     for o in outs[1:]:
         assert np.array_equal(outs[0][0], o[0])
         assert np.array_equal(outs[0][1], o[1])
-    for bad in ((3, 0, 0, 0), (0, 2, 0, 0)):
+    for bad in ((4, 0, 0, 0), (0, 2, 0, 0)):
         with pytest.raises(g.GbdError):
             g.gbd_mesh_set_tuning(mesh.handle, bad)
     mesh.close()
@@ -64,7 +65,7 @@ def test_autotune_valid_and_cached(g, tmp_path, monkeypatch):
     mesh = _mesh(g, (160, 64, 1), (2e-9, 2e-9, 3e-9), 8e5)
     v1 = mesh.autotune()
     v2 = mesh.autotune()
-    assert v1 == v2 and v1[0] in (0, 1, 2) and all(x in (0, 1) for x in v1[1:])
+    assert v1 == v2 and v1[0] in (0, 1, 2, 3) and all(x in (0, 1) for x in v1[1:])
     mesh.close()
 
 

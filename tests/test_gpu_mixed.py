@@ -62,13 +62,13 @@ def test_mixed_length_rk4_step_and_tile_variants(g, n, cell):
     mesh = g.Mesh(n, cell, Ms, A_ex=A, alpha=alpha)
     m0 = W.random_unit(n, 62)
     outs = []
-    for v in ((1, 0, 0, 0), (2, 0, 0, 0)):     # row_kernel and the pipelined kernel
+    for v in ((1, 0, 0, 0), (2, 0, 0, 0), (3, 0, 0, 0)):     # row_kernel and the pipelined kernel
         g.gbd_mesh_set_tuning(mesh.handle, v)
         md = to_dev(m0)
         mesh.llg_step(md, 2, dt)
         outs.append(to_host(md))
     mesh.close()
-    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
     Nf = T.tensor_all_offsets(n, cell)
     want = L.llg_run(m0.astype(np.float64), 2, dt, Nf, cell, Ms, A, alpha)
     assert np.abs(outs[0] - want).max() < 2e-6
