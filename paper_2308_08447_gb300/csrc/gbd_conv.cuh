@@ -143,14 +143,16 @@ __global__ void __launch_bounds__(3 * W_ * L / GBD_E,
   const long long q0 = (long long)blockIdx.x * W;
   const int nz = a.nz;
   const long long Q = a.Q;
+  const int Qi = (int)Q;   // Hx Py <= 4097 * 4096: a plane offset z Q fits in 32-bit int arithmetic
   float2* D = a.dst;
+  // element z of line (component c = line / W, column q0 + line % W): the line's base, computed
+  // once per line by the compiler, plus z Q
+  auto lbase = [&](int line) { return D + (long long)(line / W) * nz * Q + q0 + line % W; };
   auto gld = [&](int line, int z) {
-    const long long q = q0 + line % W;
-    return (z < nz && q < Q) ? D[(long long)((line / W) * nz + z) * Q + q] : make_float2(0.f, 0.f);
+    return (z < nz && q0 + line % W < Q) ? lbase(line)[(long long)z * Qi] : make_float2(0.f, 0.f);
   };
   auto gst = [&](int line, int z, float2 v) {
-    const long long q = q0 + line % W;
-    if (z < nz && q < Q) D[(long long)((line / W) * nz + z) * Q + q] = v;
+    if (z < nz && q0 + line % W < Q) lbase(line)[(long long)z * Qi] = v;
   };
   auto sld = [&](int line, int i) { return sm[line * LS + pad(i)]; };
   auto sst = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
@@ -206,16 +208,32 @@ __global__ void __launch_bounds__(3 * W_ * L / GBD_E,
     // The last forward pass, the product and the first adjoint pass as three in-place phases
     // over all threads: the last pass (Ns R = L) leaves frequency j + q L/R at the position
     // it read, so each phase touches only its own items' positions.
+    // T is a multiple of LINES, so a thread keeps one line through its 16 / RL items, and with
+    // LR a multiple of 16 an item's RL elements sit at pad(j) + r (LR + LR/16): one base address
+    // per item and compile-time offsets.
+    static_assert(T % LINES == 0 && (LINES * LR) % T == 0, "z convolution: items per thread");
     auto last_pass = [&](auto adj) {
       constexpr bool ADJ = decltype(adj)::value;
-      for (int it = threadIdx.x; it < LINES * LR; it += T) {
-        const int line = it % LINES, j = it / LINES;
+      constexpr int NI = LINES * LR / T;
+      constexpr bool NAT = (LR % 16 == 0);
+      constexpr int STRIDE = LR + LR / 16;
+      const int line = threadIdx.x % LINES;
+      const int j0 = threadIdx.x / LINES;
+#pragma unroll
+      for (int i = 0; i < NI; ++i) {
+        const int j = j0 + i * (T / LINES);
+        float2* lp = sm + line * LS + (NAT ? pad(j) : 0);
         float2 v[RL];
 #pragma unroll
-        for (int r = 0; r < RL; ++r) v[r] = sld(line, j + r * LR);
+        for (int r = 0; r < RL; ++r) v[r] = NAT ? lp[r * STRIDE] : lp[pad(j + r * LR)];
         butterfly<ADJ ? 1 : -1, RL, NSL, ADJ>(v, j, tw);
 #pragma unroll
-        for (int r = 0; r < RL; ++r) sst(line, j + r * LR, v[r]);
+        for (int r = 0; r < RL; ++r) {
+          if (NAT)
+            lp[r * STRIDE] = v[r];
+          else
+            lp[pad(j + r * LR)] = v[r];
+        }
       }
     };
     last_pass(std::false_type());
@@ -227,8 +245,8 @@ __global__ void __launch_bounds__(3 * W_ * L / GBD_E,
     static_assert(T % W == 0, "a thread's product items share one column");
     const int w = threadIdx.x % W;
     const long long q = q0 + w;
-    const int kx = (int)(q / Pyq);
-    const int ky = (int)(q - (long long)kx * Pyq);
+    const int kx = (int)q / Pyq;   // q < Q = Hx Py fits in int: 32-bit division
+    const int ky = (int)q - kx * Pyq;
     int kyp = ky;
     float sy = 1.f;
     if (Py > 1 && ky > Py / 2) {

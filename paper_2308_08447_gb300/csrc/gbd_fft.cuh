@@ -397,9 +397,13 @@ __device__ __forceinline__ void stockham_pass(const float2* __restrict__ tw, LD 
 //   scattered set (j-k) R + k + q Ns: pad = pad(base) + q (Ns + Ns/16)   when Ns % 16 == 0,
 //                                     pad = 17 j + q                      when Ns = 1, R = 16
 // (other cases compute pad per element).
-template <int S, bool ADJ, int L, int R, int Ns, int LINES, bool LF, int LS>
+// HALF (the Ns = 1 pass, even R): forward, the upper half of each line is zero -- only the
+// inputs r < R/2 are loaded and the butterfly is dft_half_in; adjoint, only the lower half of the
+// output is kept -- dft_half_out and the stores q < R/2.
+template <int S, bool ADJ, int L, int R, int Ns, int LINES, bool LF, int LS, bool HALF = false>
 __device__ __forceinline__ void stockham_pass_sm(float2* sm, const float2* __restrict__ tw) {
   static_assert(R % 2 == 0 || Ns == 1, "an odd radix is the Ns = 1 pass");
+  static_assert(!HALF || (Ns == 1 && R % 2 == 0), "the half transforms are the Ns = 1 pass of an even radix");
   constexpr int LR = L / R;
   constexpr int NB = (GBD_E + R - 1) / R;
   constexpr int T = LINES * L / GBD_E;
@@ -431,7 +435,7 @@ __device__ __forceinline__ void stockham_pass_sm(float2* sm, const float2* __res
     auto nat = [&](int r) { return NAT_CONST ? nat0[i] + r * NAT_STRIDE : lb + pad(j + r * LR); };
     auto sca = [&](int q) { return SCA_CONST ? sca0[i] + q * SCA_STRIDE : lb + pad(base + q * Ns); };
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[i][r] = sm[ADJ ? sca(r) : nat(r)];
+    for (int r = 0; r < ((HALF && !ADJ) ? R / 2 : R); ++r) v[i][r] = sm[ADJ ? sca(r) : nat(r)];
   }
   __syncthreads();
 #pragma unroll
@@ -439,11 +443,16 @@ __device__ __forceinline__ void stockham_pass_sm(float2* sm, const float2* __res
     if (NB * T != NBUT && threadIdx.x + i * T >= NBUT) continue;
     const int j = bj[i];
     const int k = j % Ns;
-    butterfly<S, R, Ns, ADJ>(v[i], k, tw);
+    if constexpr (HALF && ADJ)
+      dft_half_out<R, S>(v[i]);
+    else if constexpr (HALF)
+      dft_half_in<R, S>(v[i]);
+    else
+      butterfly<S, R, Ns, ADJ>(v[i], k, tw);
     const int lb_nat = nat0[i] - (NAT_CONST ? pad(j) : j);   // line base
     const int lb_sca = sca0[i] - (SCA_CONST ? (Ns == 1 ? 17 * j : pad((j - k) * R + k)) : (j - k) * R + k);
 #pragma unroll
-    for (int q = 0; q < R; ++q) {
+    for (int q = 0; q < ((HALF && ADJ) ? R / 2 : R); ++q) {
       int addr;
       if (ADJ)
         addr = NAT_CONST ? nat0[i] + q * NAT_STRIDE : lb_nat + pad(j + q * LR);

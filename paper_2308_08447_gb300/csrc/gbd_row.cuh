@@ -412,10 +412,13 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
         if (i < HALF) sm[line * LS + pad(i)] = v;
       };
       auto st_all = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
+      constexpr int R0 = radix_at(LX, false, 0);
       if (xper)
-        pass_any<PREC, 1, true, LX, radix_at(LX, false, 0), 1, LINES, false, true>(tw, ld, st_all);
+        pass_any<PREC, 1, true, LX, R0, 1, LINES, false, true>(tw, ld, st_all);
+      else if constexpr (PREC == 0 && R0 % 2 == 0)
+        stockham_pass_sm<1, true, LX, R0, 1, LINES, false, LS, true>(sm, tw);   // keeps the lower half
       else
-        pass_any<PREC, 1, true, LX, radix_at(LX, false, 0), 1, LINES, false, true>(tw, ld, st_half);
+        pass_any<PREC, 1, true, LX, R0, 1, LINES, false, true>(tw, ld, st_half);
       __syncthreads();
     }
     }
@@ -523,10 +526,13 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
     auto ld_half = [&](int line, int i) { return i < HALF ? sm[line * LS + pad(i)] : make_float2(0.f, 0.f); };
     auto ld_all = [&](int line, int i) { return sm[line * LS + pad(i)]; };
     auto st = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
+    constexpr int R0 = radix_at(LX, false, 0);
     if (xper)
-      pass_any<PREC, -1, false, LX, radix_at(LX, false, 0), 1, LINES, false, true>(tw, ld_all, st);
+      pass_any<PREC, -1, false, LX, R0, 1, LINES, false, true>(tw, ld_all, st);
+    else if constexpr (PREC == 0 && R0 % 2 == 0)
+      stockham_pass_sm<-1, false, LX, R0, 1, LINES, false, LS, true>(sm, tw);   // reads the lower half
     else
-      pass_any<PREC, -1, false, LX, radix_at(LX, false, 0), 1, LINES, false, true>(tw, ld_half, st);
+      pass_any<PREC, -1, false, LX, R0, 1, LINES, false, true>(tw, ld_half, st);
     __syncthreads();
     fwd_passes_smem<-1, LX, false, LINES, false, LS, 1, NP, PREC>(sm, tw);
   }

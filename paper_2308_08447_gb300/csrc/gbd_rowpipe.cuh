@@ -196,11 +196,16 @@ __global__ void __launch_bounds__(3 * pipe_rb(LX) * LX / GBD_E, pipe_blocks(K))
       // 2. unnormalised inverse FFT; the last pass keeps the lower half (the cropped rows)
       adj_passes_smem<1, LX, false, LINES, false, LS, NP, 1, 0>(lines, tw);
       {
-        auto ld = [&](int line, int i) { return lines[line * LS + pad(i)]; };
-        auto st_half = [&](int line, int i, float2 v) {
-          if (i < HALF) lines[line * LS + pad(i)] = v;
-        };
-        pass_any<0, 1, true, LX, radix_at(LX, false, 0), 1, LINES, false, true>(tw, ld, st_half);
+        constexpr int R0 = radix_at(LX, false, 0);
+        if constexpr (R0 % 2 == 0) {
+          stockham_pass_sm<1, true, LX, R0, 1, LINES, false, LS, true>(lines, tw);   // keeps the lower half
+        } else {
+          auto ld = [&](int line, int i) { return lines[line * LS + pad(i)]; };
+          auto st_half = [&](int line, int i, float2 v) {
+            if (i < HALF) lines[line * LS + pad(i)] = v;
+          };
+          pass_any<0, 1, true, LX, R0, 1, LINES, false, true>(tw, ld, st_half);
+        }
       }
       if constexpr (K == PIPE_RK)
         cp_async_wait<1>();   // this group's field rows (the next spectrum may stay in flight)
@@ -334,9 +339,14 @@ __global__ void __launch_bounds__(3 * pipe_rb(LX) * LX / GBD_E, pipe_blocks(K))
     if (pipe_rk(K) && !a.fwd_after) continue;   // uniform over the grid
     // 4. forward FFT; the first pass reads the lower half only (the upper half is zero)
     {
-      auto ld_half = [&](int line, int i) { return i < HALF ? lines[line * LS + pad(i)] : make_float2(0.f, 0.f); };
-      auto st = [&](int line, int i, float2 v) { lines[line * LS + pad(i)] = v; };
-      pass_any<0, -1, false, LX, radix_at(LX, false, 0), 1, LINES, false, true>(tw, ld_half, st);
+      constexpr int R0 = radix_at(LX, false, 0);
+      if constexpr (R0 % 2 == 0) {
+        stockham_pass_sm<-1, false, LX, R0, 1, LINES, false, LS, true>(lines, tw);   // reads the lower half
+      } else {
+        auto ld_half = [&](int line, int i) { return i < HALF ? lines[line * LS + pad(i)] : make_float2(0.f, 0.f); };
+        auto st = [&](int line, int i, float2 v) { lines[line * LS + pad(i)] = v; };
+        pass_any<0, -1, false, LX, R0, 1, LINES, false, true>(tw, ld_half, st);
+      }
       __syncthreads();
       fwd_passes_smem<-1, LX, false, LINES, false, LS, 1, NP, 0>(lines, tw);
     }
