@@ -112,15 +112,69 @@ __global__ void __launch_bounds__(3 * C_ * L / GBD_E,
   if constexpr (NP <= 1) {
     run_fused(gld, gst);
   } else {
-    // The zero half of a y line is skipped by gld / gst alone: the half transforms that the z
-    // convolution uses (HALF passes) measured 2 us slower in this 56-register kernel (spills).
-    pass_any<PREC, -1, false, L, radix_at(L, true, 0), 1, LINES, false, false>(tw, gld, sst);
+    // Radix-16 outer passes (FP32, one butterfly per thread, lines not interleaved): the thread's
+    // line and butterfly j are fixed, its global elements y = j + r L/16 of one column pointer and
+    // its shared-memory elements 16 j + q at the padded 17 j + q; with the upper half of a y line
+    // zero (2 ny <= L) the first pass is a half-input DFT and the last one computes and stores
+    // only the kept half.
+    constexpr int R0 = radix_at(L, true, 0);
+    constexpr bool FAST = (PREC == 0 && R0 == 16);
+    const int fline = threadIdx.x / (L / 16), fj = threadIdx.x % (L / 16);
+    const bool fok = kx0 + fline % C < Hx;
+    const bool half = 2 * ny <= L;
+    if constexpr (FAST) {
+      const float2* gp = gptr(fline);
+      float2 v[16];
+      if (half) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int y = fj + r * (L / 16);
+          v[r] = (fok && y < ny) ? gp[y] : make_float2(0.f, 0.f);
+        }
+        dft_half_in<16, -1>(v);
+      } else {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          const int y = fj + r * (L / 16);
+          v[r] = (fok && y < ny) ? gp[y] : make_float2(0.f, 0.f);
+        }
+        dft<16, -1>(v);
+      }
+      float2* sp = sm + fline * LS + 17 * fj;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) sp[q] = v[q];
+    } else {
+      pass_any<PREC, -1, false, L, R0, 1, LINES, false, false>(tw, gld, sst);
+    }
     __syncthreads();
     fwd_passes_smem<-1, L, true, LINES, false, LS, 1, NP - 1, PREC>(sm, tw);
     run_fused(sld, sst);
     __syncthreads();
     adj_passes_smem<1, L, true, LINES, false, LS, NP - 1, 1, PREC>(sm, tw);
-    pass_any<PREC, 1, true, L, radix_at(L, true, 0), 1, LINES, false, false>(tw, sld, gst);
+    if constexpr (FAST) {
+      const float2* sp = sm + fline * LS + 17 * fj;
+      float2 v[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = sp[r];
+      float2* gp = gptr(fline);
+      if (half) {
+        dft_half_out<16, 1>(v);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int y = fj + q * (L / 16);
+          if (fok && y < ny) gp[y] = v[q];
+        }
+      } else {
+        dft<16, 1>(v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int y = fj + q * (L / 16);
+          if (fok && y < ny) gp[y] = v[q];
+        }
+      }
+    } else {
+      pass_any<PREC, 1, true, L, R0, 1, LINES, false, false>(tw, sld, gst);
+    }
   }
 }
 
@@ -199,10 +253,31 @@ __global__ void __launch_bounds__(3 * W_ * L / GBD_E,
   } else {
     // open z (Pz >= 2 nz): zero upper half in, cropped out; periodic z (Pz = nz): whole lines
     const bool half = 2 * nz <= L;
-    if (half)
-      pass_any<PREC, -1, false, L, radix_at(L, true, 0), 1, LINES, true, false, true>(tw, gld, sst);
-    else
-      pass_any<PREC, -1, false, L, radix_at(L, true, 0), 1, LINES, true, false>(tw, gld, sst);
+    // The outer passes of a radix-16 first pass (one butterfly per thread, FP32): the thread's
+    // line and butterfly j are fixed, its global elements are z = j + r L/16 of one line base,
+    // and its shared-memory elements 16 j + q sit at 17 j + q (padded), so addresses are one base
+    // each plus constant offsets.
+    constexpr int R0 = radix_at(L, true, 0);
+    constexpr bool FAST = (PREC == 0 && R0 == 16 && T == LINES * (L / 16));
+    const int fline = threadIdx.x % LINES, fj = threadIdx.x / LINES;
+    const bool fq = q0 + fline % W < Q;
+    if (FAST && half) {
+      const float2* gp = lbase(fline);
+      float2 v[16];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int z = fj + r * (L / 16);
+        v[r] = (fq && z < nz) ? gp[(long long)z * Qi] : make_float2(0.f, 0.f);
+      }
+      dft_half_in<16, -1>(v);
+      float2* sp = sm + fline * LS + 17 * fj;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) sp[q] = v[q];
+    } else if (half) {
+      pass_any<PREC, -1, false, L, R0, 1, LINES, true, false, true>(tw, gld, sst);
+    } else {
+      pass_any<PREC, -1, false, L, R0, 1, LINES, true, false>(tw, gld, sst);
+    }
     __syncthreads();
     fwd_passes_smem<-1, L, true, LINES, true, LS, 1, NP - 1, PREC>(sm, tw);
     // The last forward pass, the product and the first adjoint pass as three in-place phases
@@ -276,10 +351,23 @@ __global__ void __launch_bounds__(3 * W_ * L / GBD_E,
     last_pass(std::true_type());
     __syncthreads();
     adj_passes_smem<1, L, true, LINES, true, LS, NP - 1, 1, PREC>(sm, tw);
-    if (half)
-      pass_any<PREC, 1, true, L, radix_at(L, true, 0), 1, LINES, true, false, true>(tw, sld, gst);
-    else
-      pass_any<PREC, 1, true, L, radix_at(L, true, 0), 1, LINES, true, false>(tw, sld, gst);
+    if (FAST && half) {
+      const float2* sp = sm + fline * LS + 17 * fj;
+      float2 v[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = sp[r];
+      dft_half_out<16, 1>(v);
+      float2* gp = lbase(fline);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int z = fj + q * (L / 16);
+        if (fq && z < nz) gp[(long long)z * Qi] = v[q];
+      }
+    } else if (half) {
+      pass_any<PREC, 1, true, L, R0, 1, LINES, true, false, true>(tw, sld, gst);
+    } else {
+      pass_any<PREC, 1, true, L, R0, 1, LINES, true, false>(tw, sld, gst);
+    }
   }
 }
 
