@@ -75,8 +75,12 @@ __global__ void __launch_bounds__(3 * C_ * L / GBD_E,
   auto sld = [&](int line, int i) { return sm[line * LS + pad(i)]; };
   auto sst = [&](int line, int i, float2 v) { sm[line * LS + pad(i)] = v; };
 
+  // An item is a butterfly position j of column cc: the coupled (x, y) pair (two lines) and the
+  // z line. When the C LR pair items leave threads over (C LR < T), the first C LR threads take
+  // the pairs and the others the z lines, so that every thread does about two lines' work.
   auto run_fused = [&](auto ld, auto st) {
-    for (int it = threadIdx.x; it < C * LR; it += T) {
+    constexpr bool SPLIT = (C * LR < T) && ((C * LR) % (T - C * LR) == 0);
+    auto item = [&](int it, bool xy, bool zz) {
       const int cc = it / LR, j = it % LR;
       const int kx = kx0 + cc;
       auto kfetch = [&](int ky, float& sy) {
@@ -104,8 +108,17 @@ __global__ void __launch_bounds__(3 * C_ * L / GBD_E,
         const float4 k4 = kfetch(ky, sy);
         m2 = make_float2(k4.z * m2.x, k4.z * m2.y);
       };
-      fused_item<L, RL, NSL, decltype(ld), decltype(st), decltype(mulxy), 2>(cc, C, j, tw, ld, st, mulxy);
-      fused_item<L, RL, NSL, decltype(ld), decltype(st), decltype(mulz), 1>(cc + 2 * C, C, j, tw, ld, st, mulz);
+      if (xy) fused_item<L, RL, NSL, decltype(ld), decltype(st), decltype(mulxy), 2>(cc, C, j, tw, ld, st, mulxy);
+      if (zz) fused_item<L, RL, NSL, decltype(ld), decltype(st), decltype(mulz), 1>(cc + 2 * C, C, j, tw, ld, st, mulz);
+    };
+    if constexpr (SPLIT) {
+      if (threadIdx.x < C * LR) {
+        item(threadIdx.x, true, false);
+      } else {
+        for (int it = threadIdx.x - C * LR; it < C * LR; it += T - C * LR) item(it, false, true);
+      }
+    } else {
+      for (int it = threadIdx.x; it < C * LR; it += T) item(it, true, true);
     }
   };
 
