@@ -82,6 +82,8 @@ struct RowArgs {
   float geff, alpha;        // gamma / (1 + alpha^2), alpha
   float dt;                 // time step, s
   int vec8;                 // the field pointers allow 8-byte accesses (set by launch_row)
+  int stage;                // the RK-stage epilogue reads its field rows from shared memory,
+                            // copied there while the inverse transform runs (set by the launcher)
   int per;                  // periodic axes (bit 0 x, 1 y, 2 z): the x transform has no zero
                             // half, and the exchange Laplacian wraps around
   // demag extrapolation at RK sub-steps (Sec. III): with extrap the stage's demag field is

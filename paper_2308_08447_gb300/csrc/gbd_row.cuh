@@ -3,11 +3,26 @@
 // the epilogue device functions and the row kernel template, shared by the translation units of
 // the FP32 kernels (gbd_row.cu) and of the split 16-bit kernels (gbd_row_bf16.cu, gbd_row_fp16.cu).
 #pragma once
+#include <cstdint>
 #include <type_traits>
 
 #include "gbd_launch.cuh"
 
 namespace gbd {
+
+// Asynchronous global -> shared copies (cp.async, 16 or 8 bytes per thread), in commit groups.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async16(void* s, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* s, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 // ---------------------------------------------------------------------------------------------
 // x rows: real-to-complex through a half-length complex FFT (Lx = Px / 2).
@@ -298,6 +313,26 @@ __device__ __forceinline__ bool epilogue_cell(const RowArgs& a, int mode, int z,
   return true;
 }
 
+// Staged RK-stage epilogue (FP32 row kernels that run one block per SM). The stage input m on
+// the block's rows and the rows above and below ([RB + 2][3][LX] floats, after the lines on a
+// 16-byte boundary) is copied into shared memory with cp.async while the inverse transform runs,
+// so the Laplacian reads shared memory; the step-start m and the k-sum (no reuse) stay in global
+// memory and are requested one item ahead. Staging them too would cost more than it saves: the
+// L1 cache shares the SM's 256 KB with shared memory, and the spectrum loads need the room.
+template <int LX, int RB>
+__host__ __device__ constexpr int row_stage_off() {   // float2 slots
+  return (3 * RB * line_stride<LX, true>() + 1) / 2 * 2;
+}
+template <int LX, int RB>
+__host__ __device__ constexpr size_t row_stage_smem() {
+  return (size_t)row_stage_off<LX, RB>() * 8 + (size_t)(RB + 2) * 3 * LX * 4;
+}
+template <int LX, int RB, int PREC>
+__host__ __device__ constexpr bool row_stage_ok() {
+  return PREC == 0 && npasses(LX, false) >= 1 && min_blocks(3 * RB * LX / GBD_E) == 1 &&
+         row_stage_smem<LX, RB>() <= 232448;
+}
+
 template <int LX, int RB_, int PREC>
 __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX / GBD_E))
     row_kernel(RowArgs a, const float2* __restrict__ tw) {
@@ -335,6 +370,27 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
   constexpr int VR = (RB % 2 == 0) ? 2 : 1;
   constexpr int RG = RB / VR;
   const bool vec = (VR == 2) && one_plane && (ny % 2 == 0);
+  // staged epilogue (a.stage: an RK stage with the next forward transform, free x boundary,
+  // nx a multiple of 64, 16-byte aligned fields)
+  constexpr bool SOK = row_stage_ok<LX, RB, PREC>();
+  const bool stg = SOK && a.stage && one_plane;
+  float* sMs = reinterpret_cast<float*>(sm + row_stage_off<LX, RB>());   // [RB + 2][3][LX]
+  // rows yb - 1 .. yb + RB of the stage input: a missing neighbour row is the row itself (free
+  // boundary) or the row on the opposite face (periodic y)
+  auto issue_stage_rows = [&]() {
+    const int nq = nx / 4;
+    const long long plane = (long long)zb * ny;
+    for (int e = threadIdx.x; e < (RB + 2) * 3 * nq; e += T) {
+      const int q = e % nq;
+      const int t2 = e / nq;
+      const int c = t2 % 3, s = t2 / 3;
+      int y = yb - 1 + s;
+      if (y < 0) y = (a.per & 2) ? ny - 1 : 0;
+      if (y >= ny) y = (a.per & 2) ? 0 : ny - 1;
+      cp_async16(sMs + (s * 3 + c) * LX + 4 * q, ms + c * N + (plane + y) * nx + 4 * q);
+    }
+    cp_async_commit();
+  };
 
   if (mode != ROW_FWD) {
     if (!a.extrap) {  // uniform over the grid
@@ -376,6 +432,10 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
           }
         }
       }
+    }
+    // the staged rows are requested behind the spectrum loads, which the next loop waits for
+    if constexpr (SOK) {
+      if (stg) issue_stage_rows();
     }
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {
@@ -422,33 +482,128 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
       __syncthreads();
     }
     }
+    if constexpr (SOK) {
+      if (stg) {
+        cp_async_wait<0>();
+        __syncthreads();
+      }
+    }
     // 3. epilogue on the real rows: float view of line position x is 2 pad(x/2) + (x & 1).
     if ((nx % 64) == 0 && a.vec8) {
       // Fast path (8-byte aligned fields): an item is a pair of cells (x0, x0 + 1); the 32
       // lanes of a warp take 32 consecutive pairs of one row (epilogue_pair).
       const int NP2 = nx / 2;
-      for (int e = threadIdx.x; e < RB * NP2; e += T) {
-        const int rr = e / NP2;
-        const int xp = e - rr * NP2;
-        if (r0 + rr >= a.rows) continue;  // uniform per warp (NP2 is a multiple of 32)
-        int z, y;
-        row_zy(rr, z, y);
-        const int x0 = 2 * xp;
-        const long long idx = (long long)(r0 + rr) * nx + x0;
-        float hd[2][3], mn[2][3];
-        if (a.extrap) {
-          extrap_pair(a, idx, hd);
-        } else {
+      bool staged = false;
+      if constexpr (SOK) {
+        if (stg) {
+          // the field rows from shared memory (one_plane: all RB rows exist, in plane zb); the
+          // arithmetic is epilogue_pair's, term for term
+          const long long sz = (long long)nx * ny;
+          const long long ozm = zb > 0 ? -sz : ((a.per & 4) ? (long long)(a.nz - 1) * sz : 0);
+          const long long ozp = zb < a.nz - 1 ? sz : ((a.per & 4) ? -(long long)(a.nz - 1) * sz : 0);
+          // the step-start m and k-sum of the next item are requested before this item's update
+          const bool rk_acc = mode != ROW_RK1;   // stages 2-4 read them
+          float2 q0n[3], qan[3];
+          auto fetch = [&](int e, float2 (&q0)[3], float2 (&qa)[3]) {
+            const int rr = e / NP2;
+            const long long idx = (long long)(r0 + rr) * nx + 2 * (e - rr * NP2);
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const float2 h2 = sm[(c * RB + rr) * LS + pad(xp)];
-            hd[0][c] = h2.x * a.hscale;
-            hd[1][c] = h2.y * a.hscale;
+            for (int c = 0; c < 3; ++c) {
+              q0[c] = *reinterpret_cast<const float2*>(a.m0 + c * N + idx);
+              qa[c] = *reinterpret_cast<const float2*>(a.acc + c * N + idx);
+            }
+          };
+          if (rk_acc && threadIdx.x < RB * NP2) fetch(threadIdx.x, q0n, qan);
+          for (int e = threadIdx.x; e < RB * NP2; e += T) {
+            const int rr = e / NP2;
+            const int xp = e - rr * NP2;
+            const int x0 = 2 * xp;
+            const long long idx = (long long)(r0 + rr) * nx + x0;
+            float hd[2][3], mv[2][3], lap[2][3], m0v[2][3] = {}, accv[2][3] = {}, mn[2][3], ao[2][3], res[2][3];
+            if (rk_acc) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                m0v[0][c] = q0n[c].x;
+                m0v[1][c] = q0n[c].y;
+                accv[0][c] = qan[c].x;
+                accv[1][c] = qan[c].y;
+              }
+              if (e + T < RB * NP2) fetch(e + T, q0n, qan);
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const float2 h2 = sm[(c * RB + rr) * LS + pad(xp)];
+              hd[0][c] = h2.x * a.hscale;
+              hd[1][c] = h2.y * a.hscale;
+            }
+            if (a.hrec) {
+#pragma unroll
+              for (int c = 0; c < 3; ++c)
+                *reinterpret_cast<float2*>(a.hrec + c * N + idx) = make_float2(hd[0][c], hd[1][c]);
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const float* rc = sMs + ((rr + 1) * 3 + c) * LX;
+              const float2 cc = *reinterpret_cast<const float2*>(rc + x0);
+              const float2 ym = *reinterpret_cast<const float2*>(sMs + (rr * 3 + c) * LX + x0);
+              const float2 yp = *reinterpret_cast<const float2*>(sMs + ((rr + 2) * 3 + c) * LX + x0);
+              const float left = x0 > 0 ? rc[x0 - 1] : cc.x;          // free x boundary
+              const float right = x0 + 2 < nx ? rc[x0 + 2] : cc.y;
+              float2 zm = cc, zp = cc;
+              if (a.nz > 1) {
+                const float* p = ms + c * N + idx;
+                zm = *reinterpret_cast<const float2*>(p + ozm);
+                zp = *reinterpret_cast<const float2*>(p + ozp);
+              }
+              mv[0][c] = cc.x;
+              mv[1][c] = cc.y;
+              lap[0][c] = a.cx * (left - 2.f * cc.x + cc.y) + a.cy * (ym.x - 2.f * cc.x + yp.x) +
+                          a.cz * (zm.x - 2.f * cc.x + zp.x);
+              lap[1][c] = a.cx * (cc.x - 2.f * cc.y + right) + a.cy * (ym.y - 2.f * cc.y + yp.y) +
+                          a.cz * (zm.y - 2.f * cc.y + zp.y);
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) llg_update(a, mode, hd[u], mv[u], lap[u], m0v[u], accv[u], mn[u], ao[u], res[u]);
+            // m0_out aliases m0 in stage 4: each cell's m0 is read, then written, by one thread
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const float2 v = make_float2(mn[0][c], mn[1][c]);
+              if (mode == ROW_RK4) {
+                *reinterpret_cast<float2*>(a.m0_out + c * N + idx) = v;
+              } else {
+                *reinterpret_cast<float2*>(a.acc + c * N + idx) = make_float2(ao[0][c], ao[1][c]);
+                *reinterpret_cast<float2*>(a.mnext + c * N + idx) = v;
+              }
+              sm[(c * RB + rr) * LS + pad(xp)] = v;
+            }
           }
+          staged = true;
         }
-        if (epilogue_pair(a, mode, z, y, idx, x0, threadIdx.x & 31, hd, mn) && a.fwd_after) {
+      }
+      if (!staged) {
+        for (int e = threadIdx.x; e < RB * NP2; e += T) {
+          const int rr = e / NP2;
+          const int xp = e - rr * NP2;
+          if (r0 + rr >= a.rows) continue;  // uniform per warp (NP2 is a multiple of 32)
+          int z, y;
+          row_zy(rr, z, y);
+          const int x0 = 2 * xp;
+          const long long idx = (long long)(r0 + rr) * nx + x0;
+          float hd[2][3], mn[2][3];
+          if (a.extrap) {
+            extrap_pair(a, idx, hd);
+          } else {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) sm[(c * RB + rr) * LS + pad(xp)] = make_float2(mn[0][c], mn[1][c]);
+            for (int c = 0; c < 3; ++c) {
+              const float2 h2 = sm[(c * RB + rr) * LS + pad(xp)];
+              hd[0][c] = h2.x * a.hscale;
+              hd[1][c] = h2.y * a.hscale;
+            }
+          }
+          if (epilogue_pair(a, mode, z, y, idx, x0, threadIdx.x & 31, hd, mn) && a.fwd_after) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sm[(c * RB + rr) * LS + pad(xp)] = make_float2(mn[0][c], mn[1][c]);
+          }
         }
       }
     } else {
@@ -583,12 +738,27 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
 
 // ---- launcher --------------------------------------------------------------------------------
 
+// Whether an RK-stage launch can take the staged epilogue (row_stage_ok instances): the next
+// forward transform follows, x is not periodic (the inverse transform leaves the upper halves of
+// the lines free), the pair path applies and the staged fields are 16-byte aligned.
+static inline bool row_stage_applies(const RowArgs& a) {
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  if (a.mode < ROW_RK1 || a.mode > ROW_RK4 || a.extrap || !a.fwd_after || (a.per & 1)) return false;
+  if (a.nx % 64 != 0 || !a.vec8 || !al16(a.ms)) return false;
+  return a.mode == ROW_RK1 || (al16(a.m0) && al16(a.acc));
+}
+
 template <int LX, int RB, int PREC>
 static void row_launch_t(const RowArgs* a, const float2* tw, cudaStream_t st) {
   constexpr int T = 3 * RB * LX / GBD_E;
+  constexpr bool SOK = row_stage_ok<LX, RB, PREC>();
   const size_t smem = (size_t)3 * RB * line_stride<LX, true>() * sizeof(float2);
-  prep(row_kernel<LX, RB, PREC>, smem);
-  if (a) row_kernel<LX, RB, PREC><<<(a->rows + RB - 1) / RB, T, smem, st>>>(*a, tw);
+  prep(row_kernel<LX, RB, PREC>, SOK ? row_stage_smem<LX, RB>() : smem);
+  if (a) {
+    RowArgs b = *a;
+    b.stage = SOK && row_stage_applies(b);
+    row_kernel<LX, RB, PREC><<<(b.rows + RB - 1) / RB, T, b.stage ? row_stage_smem<LX, RB>() : smem, st>>>(b, tw);
+  }
 }
 
 // prec < 0 (with a == nullptr) prepares both precisions

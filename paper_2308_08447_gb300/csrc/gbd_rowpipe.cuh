@@ -52,19 +52,6 @@ __host__ __device__ constexpr size_t pipe_smem() {
          (K == PIPE_RK ? (size_t)(3 * pipe_rb(LX) + 2) * 3 * LX * 4 : K == PIPE_FWD ? (size_t)pipe_rb(LX) * 3 * LX * 4 : 0);
 }
 
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void cp_async16(void* s, const void* g) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(s)), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* s, const void* g) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(s)), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 // blocks per SM: the RK stage stages its field rows and fills the SM alone; the forward-only and
 // inverse-only launches stage half as much and run two blocks per SM
 __host__ __device__ constexpr int pipe_blocks(int K) { return K == PIPE_RK ? 1 : 2; }
