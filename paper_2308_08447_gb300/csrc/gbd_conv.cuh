@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(3 * C_ * L / GBD_E,
   constexpr int LR = L / RL;
   constexpr int KY = L / 2 + 1;
   extern __shared__ float2 sm[];
+  pdl_wait_then_release();
   const int kx0 = blockIdx.x * C;
   const int ny = a.ny, Hx = a.Hx;
   float2* S = a.dst;
@@ -393,7 +394,7 @@ static void film_launch_t(const ColArgs* a, const float2* tw, cudaStream_t st) {
   constexpr int T = 3 * C * L / GBD_E;
   const size_t smem = (size_t)3 * C * line_stride<L, false>() * sizeof(float2);
   prep(film_conv_kernel<L, C, PREC>, smem);
-  if (a) film_conv_kernel<L, C, PREC><<<(a->Hx + C - 1) / C, T, smem, st>>>(*a, tw);
+  if (a) launch_pdl(film_conv_kernel<L, C, PREC>, (a->Hx + C - 1) / C, T, smem, st, *a, tw);
 }
 
 template <int L, int W, int PREC>

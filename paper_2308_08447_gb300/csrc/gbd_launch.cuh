@@ -13,6 +13,32 @@ __host__ __device__ constexpr int min_blocks(int T) { return T >= 768 ? 1 : 768 
 // 3D z convolution splits its fused pass into per-component butterflies and a product phase.
 __host__ __device__ constexpr int min_blocks_film(int T) { return T >= 1152 ? 1 : 1152 / T; }
 
+// Programmatic dependent launch (PTX griddepcontrol): the x-row and film convolution kernels are
+// launched with programmatic stream serialization, so a launch may begin while the kernel before
+// it in the stream still runs -- its blocks become resident on SMs the predecessor has left idle.
+// Every thread first waits for the predecessor grid to complete with its memory operations
+// visible; the block then allows its own successor to launch. Nothing is read or written before
+// the wait, and a successor that starts early waits the same way, so the stream order of all
+// memory accesses is unchanged.
+__device__ __forceinline__ void pdl_wait_then_release() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+template <class... P, class... A>
+static void launch_pdl(void (*k)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t st, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, static_cast<A&&>(args)...);
+}
+
 // Raises the dynamic shared-memory limit of kernel k once per (kernel, device). Meshes call
 // this for their kernels when they are created, so launches inside a stream capture find the
 // attribute already set.

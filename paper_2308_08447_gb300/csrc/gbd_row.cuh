@@ -336,6 +336,7 @@ __host__ __device__ constexpr bool row_stage_ok() {
 template <int LX, int RB_, int PREC>
 __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX / GBD_E))
     row_kernel(RowArgs a, const float2* __restrict__ tw) {
+  pdl_wait_then_release();
   constexpr int RB = RB_;
   constexpr int LINES = 3 * RB;
   constexpr int T = LINES * LX / GBD_E;
@@ -757,7 +758,7 @@ static void row_launch_t(const RowArgs* a, const float2* tw, cudaStream_t st) {
   if (a) {
     RowArgs b = *a;
     b.stage = SOK && row_stage_applies(b);
-    row_kernel<LX, RB, PREC><<<(b.rows + RB - 1) / RB, T, b.stage ? row_stage_smem<LX, RB>() : smem, st>>>(b, tw);
+    launch_pdl(row_kernel<LX, RB, PREC>, (b.rows + RB - 1) / RB, T, b.stage ? row_stage_smem<LX, RB>() : smem, st, b, tw);
   }
 }
 
