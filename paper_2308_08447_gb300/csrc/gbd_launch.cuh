@@ -13,13 +13,16 @@ __host__ __device__ constexpr int min_blocks(int T) { return T >= 768 ? 1 : 768 
 // 3D z convolution splits its fused pass into per-component butterflies and a product phase.
 __host__ __device__ constexpr int min_blocks_film(int T) { return T >= 1152 ? 1 : 1152 / T; }
 
-// Programmatic dependent launch (PTX griddepcontrol): the x-row and film convolution kernels are
-// launched with programmatic stream serialization, so a launch may begin while the kernel before
-// it in the stream still runs -- its blocks become resident on SMs the predecessor has left idle.
-// Every thread first waits for the predecessor grid to complete with its memory operations
-// visible; the block then allows its own successor to launch. Nothing is read or written before
-// the wait, and a successor that starts early waits the same way, so the stream order of all
-// memory accesses is unchanged.
+// Programmatic dependent launch (PTX griddepcontrol): the x-row kernels, the film convolution and
+// the extrapolated RK stage are launched with programmatic stream serialization, so a launch may
+// begin while the kernel before it in the stream still runs -- its blocks become resident on SMs
+// the predecessor has left idle. Every thread waits for the predecessor grid to complete with its
+// memory operations visible before it touches memory the predecessor may write; the block then
+// allows its own successor to launch. Since no block releases its successor before its own wait
+// returns, a kernel that has started finds every launch before its predecessor complete: the x-row
+// kernel's RK stages use this to request their stage input (written by the x-row launch before the
+// convolution) ahead of the wait. A successor that starts early waits the same way, so the stream
+// order of all other memory accesses is unchanged.
 __device__ __forceinline__ void pdl_wait_then_release() {
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");

@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(256) rkf_final_kernel(const RkfArgs a) {
 // epilogue alone over all cells, the demag field from the history. One thread per pair of
 // cells (nx % 64 == 0, 8-byte aligned fields) or per cell.
 __global__ void __launch_bounds__(256) extrap_stage_kernel(const RowArgs a) {
+  pdl_wait_then_release();
   const int nx = a.nx, ny = a.ny;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if ((nx % 64) == 0 && a.vec8) {
@@ -210,7 +211,7 @@ void launch_extrap_stage(const RowArgs& a0, cudaStream_t st) {
   RowArgs a = a0;
   set_vec8(a);
   const long long items = ((a.nx % 64) == 0 && a.vec8) ? (long long)a.rows * (a.nx / 2) : a.N;
-  extrap_stage_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(a);
+  launch_pdl(extrap_stage_kernel, (unsigned)((items + 255) / 256), 256, 0, st, a);
 }
 bool prepare_row(int Lx, int prec) {
   if (mixed_len(Lx)) return prec <= 0 && row_dispatch_mixed(Lx, -1, nullptr, nullptr, nullptr);

@@ -336,7 +336,6 @@ __host__ __device__ constexpr bool row_stage_ok() {
 template <int LX, int RB_, int PREC>
 __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX / GBD_E))
     row_kernel(RowArgs a, const float2* __restrict__ tw) {
-  pdl_wait_then_release();
   constexpr int RB = RB_;
   constexpr int LINES = 3 * RB;
   constexpr int T = LINES * LX / GBD_E;
@@ -392,6 +391,12 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
     }
     cp_async_commit();
   };
+  // the stage input was written by an earlier x-row launch, before the convolution this launch
+  // follows, and is complete once this block runs (gbd_launch.cuh): it is requested before the wait
+  if constexpr (SOK) {
+    if (stg) issue_stage_rows();
+  }
+  pdl_wait_then_release();
 
   if (mode != ROW_FWD) {
     if (!a.extrap) {  // uniform over the grid
@@ -433,10 +438,6 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
           }
         }
       }
-    }
-    // the staged rows are requested behind the spectrum loads, which the next loop waits for
-    if constexpr (SOK) {
-      if (stg) issue_stage_rows();
     }
 #pragma unroll
     for (int i = 0; i < IPT; ++i) {

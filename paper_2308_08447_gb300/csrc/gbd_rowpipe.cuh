@@ -60,6 +60,7 @@ __host__ __device__ constexpr bool pipe_rk(int K) { return K == PIPE_RK || K == 
 template <int LX, int K>
 __global__ void __launch_bounds__(3 * pipe_rb(LX) * LX / GBD_E, pipe_blocks(K))
     row_pipe_kernel(RowArgs a, const float2* __restrict__ tw, int ngroups) {
+  pdl_wait_then_release();
   constexpr int RB = pipe_rb(LX);
   constexpr int LINES = 3 * RB;
   constexpr int T = LINES * LX / GBD_E;
@@ -392,7 +393,7 @@ static void pipe_launch_t(const RowArgs* a, const float2* tw, cudaStream_t st) {
   const int ngroups = a->rows / pipe_rb(LX);
   const int slots = pipe_blocks(K) * nsm;
   const int grid = ngroups < slots ? ngroups : slots;
-  row_pipe_kernel<LX, K><<<grid, T, smem, st>>>(*a, tw, ngroups);
+  launch_pdl(row_pipe_kernel<LX, K>, grid, T, smem, st, *a, tw, ngroups);
 }
 
 // The kind of pipelined launch that serves a for tile variant var (2: RK stages stage their field
