@@ -632,8 +632,8 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
       }
     }
     if (!a.fwd_after) return;  // uniform over the block
-    __syncthreads();
-    // 4. zero what the forward transform reads beyond the data
+    // 4. zero what the forward transform reads beyond the data (positions the epilogue does not
+    //    touch, so the barrier before the forward transform orders both)
     for (int line = 0; line < LINES; ++line) {
       const int rr = line % RB;
       const int x0 = (r0 + rr < a.rows) ? nx : 0;
