@@ -225,8 +225,7 @@ gbd_status gbd_mesh_set_state(gbd_mesh* mesh, const void* host, size_t bytes, vo
  *     work is enqueued. Every GPU that loads the library holds this array until exit.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
  *     with that device current) and caches it; with lazy module loading that lookup may also
- *     load the library's device code, and with it the array, onto the device. Make that first
- *     call before any stream capture.
+ *     load the library's device code, and with it the array, onto the device.
  *   - All calls on a device share the one array, which keeps the last call's contents. Each
  *     call writes every scratch element before reading it, so nothing needs clearing; but
  *     calls whose work overlaps on the GPU (different streams, other meshes) race on it and
