@@ -95,8 +95,12 @@ def test_effective_field_and_rhs(g, n, cell):
     mesh.close()
 
 
+# (64, 64, 1) and (128, 64, 2): nx a multiple of 64 and ny a multiple of the x-row block's rows,
+# so the RK stages read the stage input's rows from shared memory (the 3D mesh its z neighbours
+# from global memory); the others take the global-memory epilogue
 @pytest.mark.parametrize("n,cell", [((64, 48, 1), (2e-9, 2e-9, 3e-9)), ((13, 29, 7), (3e-9, 2e-9, 2e-9)),
-                                    ((100, 37, 1), (2e-9, 2e-9, 3e-9))])
+                                    ((100, 37, 1), (2e-9, 2e-9, 3e-9)), ((64, 64, 1), (2e-9, 2e-9, 3e-9)),
+                                    ((128, 64, 2), (3e-9, 3e-9, 3e-9))])
 def test_one_rk4_step(g, n, cell):
     Ms, A, alpha, dt = 8.6e5, 1.3e-11, 0.02, 1e-13
     m = W.random_unit(n, 9)

@@ -1,7 +1,8 @@
 """Periodic boundary conditions on the GPU (GBD_FLAG_PBC_*) against the oracle's reading
 (oracle/pbc.py): the demag field, H_eff with the wrapping exchange, RK4 steps, and the circular
 shift covariance along periodic axes. Meshes cover periodic x (no zero half in the x
-transform), periodic y on the film path, periodic z on the 3D path, and all three.
+transform), periodic y on the film path, periodic z on the 3D path, and all three, and RK steps
+on a mesh whose RK stages take the staged epilogue rows (periodic y).
 """
 import numpy as np
 import pytest
@@ -54,7 +55,13 @@ def test_periodic_demag_and_heff(g, n, cell, pbc, images):
     assert e_inf(heff, B.effective_field(m64, Kg, cell, Ms, A, pbc)) <= TOL_FP32
 
 
-@pytest.mark.parametrize("n,cell,pbc,images", CASES[:5])
+# nx a multiple of 64, x not periodic and ny a multiple of the x-row block's rows: the RK stages
+# read the stage input's rows from shared memory, the rows above and below a block copied in with
+# them -- here wrapped around the periodic y
+STAGED = [((64, 64, 1), (2e-9, 2e-9, 3e-9), (False, True, False), 1)]
+
+
+@pytest.mark.parametrize("n,cell,pbc,images", CASES[:5] + STAGED)
 def test_periodic_steps_track_oracle(g, n, cell, pbc, images):
     Ms, A, alpha, dt = 8e5, 1.3e-11, 0.1, 1e-13
     m = W.random_unit(n, 62)
