@@ -315,8 +315,8 @@ __device__ __forceinline__ bool epilogue_cell(const RowArgs& a, int mode, int z,
 
 // Staged RK-stage epilogue (FP32 row kernels that run one block per SM). The stage input m on
 // the block's rows and the rows above and below ([RB + 2][3][LX] floats, after the lines on a
-// 16-byte boundary) is copied into shared memory with cp.async while the inverse transform runs,
-// so the Laplacian reads shared memory; the step-start m and the k-sum (no reuse) stay in global
+// 16-byte boundary) is copied into shared memory with cp.async, requested when the block starts
+// and waited for once after the inverse transform, so the Laplacian reads shared memory; the step-start m and the k-sum (no reuse) stay in global
 // memory and are requested one item ahead. Staging them too would cost more than it saves: the
 // L1 cache shares the SM's 256 KB with shared memory, and the spectrum loads need the room.
 template <int LX, int RB>
@@ -391,8 +391,11 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
     }
     cp_async_commit();
   };
-  // the stage input was written by an earlier x-row launch, before the convolution this launch
-  // follows, and is complete once this block runs (gbd_launch.cuh): it is requested before the wait
+  // An RK stage that takes this path is launched right after a convolution launch (the film
+  // convolution, or the 3D inverse y pass) -- or, in the autotuner's timing loop, after another
+  // RK-stage launch that does not write this one's stage input -- and its stage input was written
+  // by an x-row launch before that, so it is complete once this block runs (gbd_launch.cuh): it
+  // is requested before the wait for the preceding launch.
   if constexpr (SOK) {
     if (stg) issue_stage_rows();
   }
