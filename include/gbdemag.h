@@ -242,6 +242,18 @@ gbd_status gbd_demag_noalloc(gbd_mesh* mesh, const float* M, float* H, void* str
  * accepted. */
 gbd_status gbd_mesh_destroy(gbd_mesh* mesh);
 
+/* Status of the mesh's kernels on the device. The RK-stage x-row kernels wait for bulk copies
+ * of their stage input (TMA, completed through an mbarrier); a block that has waited
+ * 100 ms of the GPU's clock gives up, ORs a flag into the mesh's device status word and carries
+ * on with what the copy has delivered, so no launch can hang and the context stays usable, but
+ * the results of the steps since the last check are not to be trusted. This call reads the
+ * word after the work queued on `stream` (NULL: the legacy default stream) so far, waits for
+ * it on the host, clears it, and returns GBD_ETIMEOUT if a wait gave up, else GBD_OK. The
+ * test hook GBD_TEST_WAIT_TIMEOUT=1 in the environment when a mesh is created makes its staged
+ * copies announce 16 bytes more than they deliver, so every such wait runs out.
+ * Errors: GBD_EINVAL (NULL mesh), GBD_ECUDA. */
+gbd_status gbd_mesh_device_status(gbd_mesh* mesh, void* stream);
+
 /* Message of the calling thread's last failure ("" if none). Valid until its next call. */
 const char* gbd_last_error(void);
 

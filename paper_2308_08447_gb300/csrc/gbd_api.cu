@@ -45,6 +45,8 @@ struct gbd_mesh {
   float* bufA = nullptr;
   float* bufB = nullptr;
   float2* tw = nullptr;     // twiddle levels, 2 GBD_TW_LEN entries
+  unsigned* status = nullptr;   // device status word (GBD_DEV_*), the 16 bytes after the twiddles
+  unsigned stage_extra = 0;     // test hook GBD_TEST_WAIT_TIMEOUT (RowArgs::stage_extra)
   // demag history for extrapolation at RK4 sub-steps: 5 slots of [3][N], allocated on the
   // first gbd_llg_step_ex with GBD_STEP_EXTRAP; hist_head = newest slot
   float* hist = nullptr;
@@ -190,7 +192,7 @@ bool make_plan(int nx, int ny, int nz, int per, bool mixed, Plan& p, const char*
   p.bytes_T = (!p.film && ny > 1) ? (size_t)3 * nz * p.Hx * p.Py * sizeof(float2) : 0;
   p.bytes_K = p.film ? (size_t)p.Hx * p.Ky * sizeof(float4) : (size_t)p.Hx * p.Ky * p.Kz * 6 * sizeof(float);
   p.bytes_state = (size_t)3 * 3 * p.N * sizeof(float);
-  p.bytes_tw = (size_t)GBD_TW_TOTAL * sizeof(float2);
+  p.bytes_tw = (size_t)(GBD_TW_TOTAL + 2) * sizeof(float2);   // + the 16-byte device status word
   return true;
 }
 
@@ -284,6 +286,7 @@ static void free_mesh_buffers(gbd_mesh* m) {
   m->K = nullptr;
   m->acc = m->bufA = m->bufB = nullptr;
   m->tw = nullptr;
+  m->status = nullptr;
 }
 
 // Records the end of the work just enqueued for m on st (not inside a stream capture: captured
@@ -327,6 +330,8 @@ static gbd::RowArgs row_args(const gbd_mesh* m) {
   a.rows = p.ny * p.nz;
   a.N = p.N;
   a.S = m->S;
+  a.status = m->status;
+  a.stage_extra = m->stage_extra;
   const double mu0 = 4.0e-7 * 3.14159265358979323846;
   const double lex = 2.0 * d.A_ex / (mu0 * d.Ms);
   a.cx = p.nx > 1 ? (float)(lex / (d.dx * d.dx)) : 0.f;
@@ -510,7 +515,13 @@ gbd_status gbd_mesh_create(const gbd_mesh_desc* desc, gbd_mesh** out) {
   for (int N = 3; N <= GBD_TW3_MAX; N *= 2) level(N);
   for (int N = 5; N <= GBD_TW5_MAX; N *= 2) level(N);
   cudaStream_t ls = lib_stream(m->device);
-  e = cudaMemcpyAsync(m->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, ls);
+  m->status = reinterpret_cast<unsigned*>(m->tw + GBD_TW_TOTAL);
+  // test hook: GBD_TEST_WAIT_TIMEOUT=1 makes this mesh's staged RK-stage copies expect 16 bytes
+  // more than they deliver, so the kernels' bounded waits run out (exercises the timeout path)
+  const char* wait_env = std::getenv("GBD_TEST_WAIT_TIMEOUT");
+  m->stage_extra = (wait_env && std::atoi(wait_env) != 0) ? 16u : 0u;
+  e = cudaMemsetAsync(m->status, 0, 16, ls);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, ls);
   if (e == cudaSuccess) {
     gbd::launch_dft16_frags(m->tw + 2 * GBD_TW_LEN, ls);
     e = cudaStreamSynchronize(ls);
@@ -580,6 +591,20 @@ gbd_status gbd_mesh_set_params(gbd_mesh* m, const double Hext[3], double alpha) 
     for (int c = 0; c < 3; ++c) m->d.Hext[c] = Hext[c];
   if (alpha >= 0) m->d.alpha = alpha;
   ++m->version;
+  return GBD_OK;
+}
+
+gbd_status gbd_mesh_device_status(gbd_mesh* m, void* stream) {
+  if (!m) return fail(GBD_EINVAL, "mesh is NULL");
+  gbd_status s = check_device(m);
+  if (s != GBD_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, m->status, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->status, 0, sizeof(h), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "device status");
+  if (h & GBD_DEV_WAIT_TIMEOUT) return fail(GBD_ETIMEOUT, "a kernel's wait for its staged copies gave up");
   return GBD_OK;
 }
 

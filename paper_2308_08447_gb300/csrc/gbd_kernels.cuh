@@ -84,6 +84,10 @@ struct RowArgs {
   int vec8;                 // the field pointers allow 8-byte accesses (set by launch_row)
   int stage;                // the RK-stage epilogue reads its field rows from shared memory,
                             // copied there while the inverse transform runs (set by the launcher)
+  unsigned* status;         // the mesh's device status word: a wait that gives up ORs in
+                            // GBD_DEV_WAIT_TIMEOUT (may be null)
+  unsigned stage_extra;     // test hook: bytes the staged copy is expected to deliver beyond what
+                            // it copies, so that its bounded wait runs out (0 in normal use)
   int per;                  // periodic axes (bit 0 x, 1 y, 2 z): the x transform has no zero
                             // half, and the exchange Laplacian wraps around
   // demag extrapolation at RK sub-steps (Sec. III): with extrap the stage's demag field is
@@ -140,6 +144,11 @@ struct ColArgs {
   long long Q;              // z-conv columns per plane = Hx * Py (Hx when ny == 1)
   int Pyq;                  // y extent of the column index q (Py, or 1 when ny == 1)
 };
+
+// Bits of a mesh's device status word (gbd_mesh_device_status).
+#define GBD_DEV_WAIT_TIMEOUT 1u
+// Longest wait of a block for its staged copies, in ns of the GPU's global timer.
+#define GBD_WAIT_LIMIT_NS 100000000ull
 
 // Launchers dispatch on the transform length (a power of two) and the tile variant; they
 // return false for a length without an instantiation.

@@ -10,6 +10,46 @@
 
 namespace gbd {
 
+// One-dimensional bulk copies global -> shared (TMA, cp.async.bulk) completed through an mbarrier
+// in shared memory: one thread initialises the barrier, announces the bytes to expect and issues
+// the copies; every thread that needs the data waits for the barrier's phase, for at most
+// limit_ns of the GPU's global timer (false when it gave up).
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"((unsigned)__cvta_generic_to_shared(b)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"((unsigned)__cvta_generic_to_shared(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(bytes), "r"((unsigned)__cvta_generic_to_shared(b))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity, unsigned long long limit_ns) {
+  const unsigned addr = (unsigned)__cvta_generic_to_shared(b);
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+}
+
 // Asynchronous global -> shared copies (cp.async, 16 or 8 bytes per thread), in commit groups.
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void cp_async16(void* s, const void* g) {
@@ -315,8 +355,10 @@ __device__ __forceinline__ bool epilogue_cell(const RowArgs& a, int mode, int z,
 
 // Staged RK-stage epilogue (FP32 row kernels that run one block per SM). The stage input m on
 // the block's rows and the rows above and below ([RB + 2][3][LX] floats, after the lines on a
-// 16-byte boundary) is copied into shared memory with cp.async, requested when the block starts
-// and waited for once after the inverse transform, so the Laplacian reads shared memory; the step-start m and the k-sum (no reuse) stay in global
+// 16-byte boundary) is copied into shared memory by one thread's bulk copies (one per row and
+// component), requested when the block starts and waited for once after the inverse transform
+// (a bounded wait: a block that gives up records GBD_DEV_WAIT_TIMEOUT in the mesh's status word
+// and carries on), so the Laplacian reads shared memory; the step-start m and the k-sum (no reuse) stay in global
 // memory and are requested one item ahead. Staging them too would cost more than it saves: the
 // L1 cache shares the SM's 256 KB with shared memory, and the spectrum loads need the room.
 template <int LX, int RB>
@@ -325,7 +367,7 @@ __host__ __device__ constexpr int row_stage_off() {   // float2 slots
 }
 template <int LX, int RB>
 __host__ __device__ constexpr size_t row_stage_smem() {
-  return (size_t)row_stage_off<LX, RB>() * 8 + (size_t)(RB + 2) * 3 * LX * 4;
+  return (size_t)row_stage_off<LX, RB>() * 8 + (size_t)(RB + 2) * 3 * LX * 4 + 16;   // + the mbarrier
 }
 template <int LX, int RB, int PREC>
 __host__ __device__ constexpr bool row_stage_ok() {
@@ -375,21 +417,22 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
   constexpr bool SOK = row_stage_ok<LX, RB, PREC>();
   const bool stg = SOK && a.stage && one_plane;
   float* sMs = reinterpret_cast<float*>(sm + row_stage_off<LX, RB>());   // [RB + 2][3][LX]
+  unsigned long long* sbar = reinterpret_cast<unsigned long long*>(sMs + (RB + 2) * 3 * LX);  // after the rows
   // rows yb - 1 .. yb + RB of the stage input: a missing neighbour row is the row itself (free
   // boundary) or the row on the opposite face (periodic y)
   auto issue_stage_rows = [&]() {
-    const int nq = nx / 4;
-    const long long plane = (long long)zb * ny;
-    for (int e = threadIdx.x; e < (RB + 2) * 3 * nq; e += T) {
-      const int q = e % nq;
-      const int t2 = e / nq;
-      const int c = t2 % 3, s = t2 / 3;
-      int y = yb - 1 + s;
-      if (y < 0) y = (a.per & 2) ? ny - 1 : 0;
-      if (y >= ny) y = (a.per & 2) ? 0 : ny - 1;
-      cp_async16(sMs + (s * 3 + c) * LX + 4 * q, ms + c * N + (plane + y) * nx + 4 * q);
+    if (threadIdx.x == 0) {
+      mbar_init(sbar, 1);
+      mbar_expect_tx(sbar, (unsigned)((RB + 2) * 3 * nx * 4) + a.stage_extra);
+      const long long plane = (long long)zb * ny;
+      for (int s = 0; s < RB + 2; ++s) {
+        int y = yb - 1 + s;
+        if (y < 0) y = (a.per & 2) ? ny - 1 : 0;
+        if (y >= ny) y = (a.per & 2) ? 0 : ny - 1;
+        for (int c = 0; c < 3; ++c)
+          bulk_g2s(sMs + (s * 3 + c) * LX, ms + c * N + (plane + y) * nx, (unsigned)(nx * 4), sbar);
+      }
     }
-    cp_async_commit();
   };
   // An RK stage that takes this path is launched right after a convolution launch (the film
   // convolution, or the 3D inverse y pass) -- or, in the autotuner's timing loop, after another
@@ -488,10 +531,7 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
     }
     }
     if constexpr (SOK) {
-      if (stg) {
-        cp_async_wait<0>();
-        __syncthreads();
-      }
+      if (stg && !mbar_wait(sbar, 0, GBD_WAIT_LIMIT_NS) && a.status) atomicOr(a.status, GBD_DEV_WAIT_TIMEOUT);
     }
     // 3. epilogue on the real rows: float view of line position x is 2 pad(x/2) + (x & 1).
     if ((nx % 64) == 0 && a.vec8) {

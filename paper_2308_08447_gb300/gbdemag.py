@@ -57,6 +57,7 @@ _SIG = {
     "gbd_llg_run_rkf56": [_P, _P, _D, ctypes.POINTER(_D), _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.c_uint,
                           _P],
     "gbd_mesh_destroy": [_P],
+    "gbd_mesh_device_status": [_P, _P],
     "gbd_tensor_at": [ctypes.POINTER(gbd_mesh_desc), _I, _I, _I, ctypes.POINTER(_D)],
     "gbd_plan_dims": [ctypes.POINTER(gbd_mesh_desc), ctypes.POINTER(_I)],
     "gbd_kernel_spectrum_host": [ctypes.POINTER(gbd_mesh_desc), ctypes.POINTER(_D), ctypes.c_size_t],
@@ -256,6 +257,15 @@ def gbd_mesh_destroy(mesh):
     _check(load().gbd_mesh_destroy(mesh))
 
 
+def gbd_mesh_device_status(mesh, stream=None):
+    """GBD_OK, or GBD_ETIMEOUT when a kernel's bounded wait gave up since the last call (the
+    word is cleared); other failures raise."""
+    s = load().gbd_mesh_device_status(mesh, _stream_ptr(stream))
+    if s not in (GBD_OK, GBD_ETIMEOUT):
+        _check(s)
+    return s
+
+
 def gbd_mesh_autotune(mesh, stream=None):
     _check(load().gbd_mesh_autotune(mesh, _stream_ptr(stream)))
 
@@ -415,6 +425,9 @@ class Mesh:
     def autotune(self, stream=None):
         gbd_mesh_autotune(self.handle, stream)
         return gbd_mesh_get_tuning(self.handle)
+
+    def device_status(self, stream=None):
+        return gbd_mesh_device_status(self.handle, stream)
 
     def close(self):
         if self.handle is not None:

@@ -83,7 +83,7 @@ def test_mesh_bytes_counts_buffers(g):
     state = 9 * N * 4
     # power-of-two levels up to 8192; split DFT-16 fragments; levels 3 * 2^j (up to 6144) and
     # 5 * 2^j (up to 5120)
-    twiddles = 2 * 8192 * 8 + 4 * 32 * 32 * 4 + 2 * 6144 * 8 + 2 * 5120 * 8
+    twiddles = 2 * 8192 * 8 + 4 * 32 * 32 * 4 + 2 * 6144 * 8 + 2 * 5120 * 8 + 16   # + device status word
     assert b == S + K + state + twiddles
 
 
