@@ -358,9 +358,10 @@ __device__ __forceinline__ bool epilogue_cell(const RowArgs& a, int mode, int z,
 // 16-byte boundary) is copied into shared memory by one thread's bulk copies (one per row and
 // component), requested when the block starts and waited for once after the inverse transform
 // (a bounded wait: a block that gives up records GBD_DEV_WAIT_TIMEOUT in the mesh's status word
-// and carries on), so the Laplacian reads shared memory; the step-start m and the k-sum (no reuse) stay in global
-// memory and are requested one item ahead. Staging them too would cost more than it saves: the
-// L1 cache shares the SM's 256 KB with shared memory, and the spectrum loads need the room.
+// and carries on), so the Laplacian reads shared memory; the step-start m and the k-sum (no
+// reuse) stay in global memory and are requested one item ahead. Staging them too would cost more
+// than it saves: the L1 cache shares the SM's 256 KB with shared memory, and the spectrum loads
+// need the room.
 template <int LX, int RB>
 __host__ __device__ constexpr int row_stage_off() {   // float2 slots
   return (3 * RB * line_stride<LX, true>() + 1) / 2 * 2;
@@ -784,8 +785,8 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
 // ---- launcher --------------------------------------------------------------------------------
 
 // Whether an RK-stage launch can take the staged epilogue (row_stage_ok instances): the next
-// forward transform follows, x is not periodic (the inverse transform leaves the upper halves of
-// the lines free), the pair path applies and the staged fields are 16-byte aligned.
+// forward transform follows, x is not periodic (the staged Laplacian takes the free x boundary),
+// the pair path applies, and the fields are 16-byte aligned (the bulk copies' sources).
 static inline bool row_stage_applies(const RowArgs& a) {
   auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
   if (a.mode < ROW_RK1 || a.mode > ROW_RK4 || a.extrap || !a.fwd_after || (a.per & 1)) return false;
