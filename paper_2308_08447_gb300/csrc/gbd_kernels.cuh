@@ -173,6 +173,10 @@ bool launch_y_fwd(int var, int prec, const ColArgs& a, const float2* tw, cudaStr
 bool launch_y_inv(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st);
 bool launch_z_conv(int var, int prec, const ColArgs& a, const float2* tw, cudaStream_t st);
 
+// The transform-only x-row instances (row kernel KIND 1, FP32, power-of-two Lx; gbd_row_io.cu):
+// launches (a == nullptr: prepares) the instance with RB rows per block; false when there is none.
+bool row_io_dispatch(int Lx, int RB, const RowArgs* a, const float2* tw, cudaStream_t st);
+
 // Transform lengths 3 * 2^k and 5 * 2^k (FP32 only; gbd_mixed_row.cu, gbd_mixed_conv.cu):
 // the launchers above forward them here. a == nullptr prepares without launching. False for
 // a length without an instantiation.

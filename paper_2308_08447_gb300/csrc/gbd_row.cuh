@@ -376,8 +376,16 @@ __host__ __device__ constexpr bool row_stage_ok() {
          row_stage_smem<LX, RB>() <= 232448;
 }
 
-template <int LX, int RB_, int PREC>
-__global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX / GBD_E))
+// Blocks per SM of the transform-only instances (KIND 1: ROW_FWD and ROW_H without demag
+// extrapolation): without the LLG epilogue a 384-thread block fits 56 registers, so three run per
+// SM instead of two.
+__host__ __device__ constexpr int io_blocks(int T) { return T >= 768 ? 1 : (T >= 384 ? 3 : 1152 / T); }
+
+// KIND 0 serves every RowMode; KIND 1 only the transform-only launches (the forward transform,
+// and the inverse transform to hscale * H_d), compiled without the epilogue's LLG code.
+template <int LX, int RB_, int PREC, int KIND = 0>
+__global__ void __launch_bounds__(3 * RB_ * LX / GBD_E,
+                                  KIND == 1 ? io_blocks(3 * RB_ * LX / GBD_E) : min_blocks(3 * RB_ * LX / GBD_E))
     row_kernel(RowArgs a, const float2* __restrict__ tw) {
   constexpr int RB = RB_;
   constexpr int LINES = 3 * RB;
@@ -415,7 +423,7 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
   const bool vec = (VR == 2) && one_plane && (ny % 2 == 0);
   // staged epilogue (a.stage: an RK stage with the next forward transform, free x boundary,
   // nx a multiple of 64, 16-byte aligned fields)
-  constexpr bool SOK = row_stage_ok<LX, RB, PREC>();
+  constexpr bool SOK = KIND == 0 && row_stage_ok<LX, RB, PREC>();
   const bool stg = SOK && a.stage && one_plane;
   float* sMs = reinterpret_cast<float*>(sm + row_stage_off<LX, RB>());   // [RB + 2][3][LX]
   unsigned long long* sbar = reinterpret_cast<unsigned long long*>(sMs + (RB + 2) * 3 * LX);  // after the rows
@@ -446,7 +454,7 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
   pdl_wait_then_release();
 
   if (mode != ROW_FWD) {
-    if (!a.extrap) {  // uniform over the grid
+    if (KIND == 1 || !a.extrap) {  // uniform over the grid
     // 1. X (global, [kx][y] layout) -> Z pairwise into shared memory. An item is (row group,
     //    component, k) with VR adjacent rows per group, read as one 16-byte vector when the
     //    rows are adjacent in memory; every thread issues all its loads before using any.
@@ -636,6 +644,16 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
           const int x0 = 2 * xp;
           const long long idx = (long long)(r0 + rr) * nx + x0;
           float hd[2][3], mn[2][3];
+          if constexpr (KIND == 1) {   // ROW_H: out = hscale * H_d (and the history record)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const float2 h2 = sm[(c * RB + rr) * LS + pad(xp)];
+              const float2 v = make_float2(h2.x * a.hscale, h2.y * a.hscale);
+              if (a.hrec) *reinterpret_cast<float2*>(a.hrec + c * N + idx) = v;
+              *reinterpret_cast<float2*>(a.out + c * N + idx) = v;
+            }
+            continue;
+          }
           if (a.extrap) {
             extrap_pair(a, idx, hd);
           } else {
@@ -663,6 +681,15 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E, min_blocks(3 * RB_ * LX 
         const long long idx = (long long)(r0 + rr) * nx + x;
         const int fpos = 2 * pad(x >> 1) + (x & 1);
         float hd[3], mn[3];
+        if constexpr (KIND == 1) {   // ROW_H
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float v = reinterpret_cast<const float*>(sm + (c * RB + rr) * LS)[fpos] * a.hscale;
+            if (a.hrec) a.hrec[c * N + idx] = v;
+            a.out[c * N + idx] = v;
+          }
+          continue;
+        }
         if (a.extrap) {
           extrap_cell(a, idx, hd);
         } else {
@@ -799,12 +826,20 @@ static void row_launch_t(const RowArgs* a, const float2* tw, cudaStream_t st) {
   constexpr int T = 3 * RB * LX / GBD_E;
   constexpr bool SOK = row_stage_ok<LX, RB, PREC>();
   const size_t smem = (size_t)3 * RB * line_stride<LX, true>() * sizeof(float2);
+  // transform-only launches of the FP32 power-of-two lengths take the KIND 1 instances
+  // (gbd_row_io.cu)
+  constexpr bool IO = PREC == 0 && !mixed_len(LX);
   prep(row_kernel<LX, RB, PREC>, SOK ? row_stage_smem<LX, RB>() : smem);
-  if (a) {
-    RowArgs b = *a;
-    b.stage = SOK && row_stage_applies(b);
-    launch_pdl(row_kernel<LX, RB, PREC>, (b.rows + RB - 1) / RB, T, b.stage ? row_stage_smem<LX, RB>() : smem, st, b, tw);
+  if (!a) {
+    if constexpr (IO) row_io_dispatch(LX, RB, nullptr, nullptr, nullptr);
+    return;
   }
+  RowArgs b = *a;
+  b.stage = SOK && row_stage_applies(b);
+  if constexpr (IO) {
+    if ((b.mode == ROW_FWD || (b.mode == ROW_H && !b.extrap)) && row_io_dispatch(LX, RB, &b, tw, st)) return;
+  }
+  launch_pdl(row_kernel<LX, RB, PREC>, (b.rows + RB - 1) / RB, T, b.stage ? row_stage_smem<LX, RB>() : smem, st, b, tw);
 }
 
 // prec < 0 (with a == nullptr) prepares both precisions
