@@ -1,7 +1,7 @@
 """FP64 CPU oracle for the demagnetizing-field convolution and the LLG/RK4 step.
 
 TEST INFRASTRUCTURE ONLY. This package is the slow, plain reference that the
-CUDA path is judged against. Only ``tests/``, ``__graft_entry__.smoke()`` and
+CUDA path is checked against. Only ``tests/``, ``__graft_entry__.smoke()`` and
 the CPU-baseline leg of ``bench.py`` may import it; the library
 (``paper_2308_08447_gb300``) never does, and this package imports nothing from
 the library. The two share no code: the library has its own FP64 tensor
