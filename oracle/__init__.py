@@ -2,7 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY. This package is the slow, plain reference that the
 CUDA path is checked against. Only ``tests/``, ``__graft_entry__.smoke()`` and
-the CPU-baseline leg of ``bench.py`` may import it; the library
+``bench.py`` -- its CPU-baseline and reference legs, and the error checks it reports
+beside the 3D and switching timings -- may import it; the library
 (``paper_2308_08447_gb300``) never does, and this package imports nothing from
 the library. The two share no code: the library has its own FP64 tensor
 generator and FFT, written separately.
