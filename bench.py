@@ -300,6 +300,8 @@ def run_ours(args):
                   "gcell_demag_per_s": round(world * cells * evals * args.steps / xt_max / 1e9, 3),
                   "max_abs_dm_vs_exact_after_%d_steps" % nsteps: float((a_ - b_).abs().max())}
 
+    # bounded device-side waits that gave up during the runs above (after the timed regions)
+    dev_status = "ok" if mesh.device_status() == gbdemag.GBD_OK else "a staged-copy wait gave up"
     result = None
     if rank == 0:
         result = {
@@ -317,6 +319,7 @@ def run_ours(args):
             "clocks": clocks,
             "roofline": roofline,
         }
+        result["device_status"] = dev_status
         if extrap is not None:
             result["extrapolated_demag"] = extrap
         if world == 1 and not args.no_cpu_baseline:
