@@ -43,7 +43,7 @@ typedef enum {
   GBD_ENOMEM = 2,       /* device or host allocation failed */
   GBD_ECUDA = 3,        /* a CUDA call failed (launch error, sticky fault, wrong device) */
   GBD_ESTATE = 4,       /* call order: e.g. gbd_demag before gbd_set_kernel */
-  GBD_ETIMEOUT = 5,     /* a bounded device-side wait gave up (batched path) */
+  GBD_ETIMEOUT = 5,     /* a bounded device-side wait gave up (gbd_mesh_device_status) */
   GBD_EBUDGET = 6,      /* admission refused: the request does not fit the memory budget */
   GBD_EUNSUPPORTED = 7  /* mesh size or transform length without a kernel, or a call the mesh cannot take */
 } gbd_status;
