@@ -146,7 +146,7 @@ def kernel_source_hash():
     """Hash of the kernel sources with // comments and blank lines left out, so that a comment
     edit does not separate the sources from counters taken on them."""
     h = hashlib.sha256()
-    for f in ("gbd_fft.cuh", "gbd_tc.cuh", "gbd_kernels.cuh", "gbd_launch.cuh", "gbd_row.cuh", "gbd_row.cu", "gbd_row_io.cu",
+    for f in ("gbd_fft.cuh", "gbd_tc.cuh", "gbd_kernels.cuh", "gbd_launch.cuh", "gbd_row.cuh", "gbd_row.cu", "gbd_row_io.cu", "gbd_row_rk.cu",
               "gbd_rowpipe.cuh", "gbd_conv.cuh", "gbd_conv.cu", "gbd_ypass.cuh", "gbd_ypass.cu", "gbd_mixed_row.cu",
               "gbd_mixed_conv.cu"):
         with open(os.path.join(ROOT, "paper_2308_08447_gb300", "csrc", f), encoding="utf-8") as fh:

@@ -18,8 +18,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbdemag.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CUDA_UNITS = ["gbd_api.cu", "gbd_row.cu", "gbd_row_io.cu", "gbd_row_bf16.cu", "gbd_row_fp16.cu", "gbd_conv.cu",
-              "gbd_conv_bf16.cu", "gbd_conv_fp16.cu", "gbd_ypass.cu", "gbd_mixed_row.cu", "gbd_mixed_conv.cu"]
+CUDA_UNITS = ["gbd_api.cu", "gbd_row.cu", "gbd_row_io.cu", "gbd_row_rk.cu", "gbd_row_bf16.cu", "gbd_row_fp16.cu",
+              "gbd_conv.cu", "gbd_conv_bf16.cu", "gbd_conv_fp16.cu", "gbd_ypass.cu", "gbd_mixed_row.cu",
+              "gbd_mixed_conv.cu"]
 CXX_UNITS = ["gbd_tensor.cpp"]
 
 

@@ -176,6 +176,8 @@ bool launch_z_conv(int var, int prec, const ColArgs& a, const float2* tw, cudaSt
 // The transform-only x-row instances (row kernel KIND 1, FP32, power-of-two Lx; gbd_row_io.cu):
 // launches (a == nullptr: prepares) the instance with RB rows per block; false when there is none.
 bool row_io_dispatch(int Lx, int RB, const RowArgs* a, const float2* tw, cudaStream_t st);
+// The staged RK-stage instances (row kernel KIND 2, FP32, power-of-two Lx; gbd_row_rk.cu), likewise.
+bool row_rk_dispatch(int Lx, int RB, const RowArgs* a, const float2* tw, cudaStream_t st);
 
 // Transform lengths 3 * 2^k and 5 * 2^k (FP32 only; gbd_mixed_row.cu, gbd_mixed_conv.cu):
 // the launchers above forward them here. a == nullptr prepares without launching. False for

@@ -382,7 +382,10 @@ __host__ __device__ constexpr bool row_stage_ok() {
 __host__ __device__ constexpr int io_blocks(int T) { return T >= 768 ? 1 : (T >= 384 ? 3 : 1152 / T); }
 
 // KIND 0 serves every RowMode; KIND 1 only the transform-only launches (the forward transform,
-// and the inverse transform to hscale * H_d), compiled without the epilogue's LLG code.
+// and the inverse transform to hscale * H_d), compiled without the epilogue's LLG code; KIND 2
+// only the staged RK stages (a.stage set, every block's rows in one z plane, ny even), compiled
+// with the branches those launches never take (extrapolation, periodic x, unvectorised spectrum
+// and epilogue paths, the unstaged epilogue) left out.
 template <int LX, int RB_, int PREC, int KIND = 0>
 __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E,
                                   KIND == 1 ? io_blocks(3 * RB_ * LX / GBD_E) : min_blocks(3 * RB_ * LX / GBD_E))
@@ -396,12 +399,12 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E,
   constexpr int HALF = LX / 2;
   constexpr int FL = NP >= 1 ? LX : 2 * LX;    // real samples the forward transform reads
   // periodic x (Px = nx, no zero padding): the whole line holds data
-  const bool xper = (a.per & 1) != 0;
+  const bool xper = KIND == 2 ? false : (a.per & 1) != 0;
   const int flr = xper ? 2 * LX : FL;          // real samples of a line that hold data or zeros
   extern __shared__ float2 sm[];
   const int r0 = blockIdx.x * RB;
   const long long N = a.N;
-  const int mode = a.mode;
+  const int mode = a.mode;   // KIND 2: an RK stage
   const int nx = a.nx, ny = a.ny;
   // (z, y) of the block's first row; when the block's rows share a z plane (ny a multiple
   // of RB, always for the power-of-two meshes) the per-element division is skipped
@@ -420,11 +423,12 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E,
   // rows per vector access of the [kx][y] spectrum: two adjacent rows are one 16-byte access
   constexpr int VR = (RB % 2 == 0) ? 2 : 1;
   constexpr int RG = RB / VR;
-  const bool vec = (VR == 2) && one_plane && (ny % 2 == 0);
+  static_assert(KIND != 2 || VR == 2, "the staged RK-stage instances read row pairs as 16-byte vectors");
+  const bool vec = KIND == 2 ? true : (VR == 2) && one_plane && (ny % 2 == 0);
   // staged epilogue (a.stage: an RK stage with the next forward transform, free x boundary,
   // nx a multiple of 64, 16-byte aligned fields)
-  constexpr bool SOK = KIND == 0 && row_stage_ok<LX, RB, PREC>();
-  const bool stg = SOK && a.stage && one_plane;
+  constexpr bool SOK = KIND != 1 && row_stage_ok<LX, RB, PREC>();
+  const bool stg = KIND == 2 ? true : SOK && a.stage && one_plane;
   float* sMs = reinterpret_cast<float*>(sm + row_stage_off<LX, RB>());   // [RB + 2][3][LX]
   unsigned long long* sbar = reinterpret_cast<unsigned long long*>(sMs + (RB + 2) * 3 * LX);  // after the rows
   // rows yb - 1 .. yb + RB of the stage input: a missing neighbour row is the row itself (free
@@ -453,8 +457,8 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E,
   }
   pdl_wait_then_release();
 
-  if (mode != ROW_FWD) {
-    if (KIND == 1 || !a.extrap) {  // uniform over the grid
+  if (KIND == 2 || mode != ROW_FWD) {
+    if (KIND != 0 || !a.extrap) {  // uniform over the grid
     // 1. X (global, [kx][y] layout) -> Z pairwise into shared memory. An item is (row group,
     //    component, k) with VR adjacent rows per group, read as one 16-byte vector when the
     //    rows are adjacent in memory; every thread issues all its loads before using any.
@@ -543,7 +547,7 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E,
       if (stg && !mbar_wait(sbar, 0, GBD_WAIT_LIMIT_NS) && a.status) atomicOr(a.status, GBD_DEV_WAIT_TIMEOUT);
     }
     // 3. epilogue on the real rows: float view of line position x is 2 pad(x/2) + (x & 1).
-    if ((nx % 64) == 0 && a.vec8) {
+    if (KIND == 2 || ((nx % 64) == 0 && a.vec8)) {
       // Fast path (8-byte aligned fields): an item is a pair of cells (x0, x0 + 1); the 32
       // lanes of a warp take 32 consecutive pairs of one row (epilogue_pair).
       const int NP2 = nx / 2;
@@ -702,7 +706,7 @@ __global__ void __launch_bounds__(3 * RB_ * LX / GBD_E,
         }
       }
     }
-    if (!a.fwd_after) return;  // uniform over the block
+    if (KIND != 2 && !a.fwd_after) return;  // uniform over the block
     // 4. zero what the forward transform reads beyond the data (positions the epilogue does not
     //    touch, so the barrier before the forward transform orders both)
     for (int line = 0; line < LINES; ++line) {
@@ -831,13 +835,18 @@ static void row_launch_t(const RowArgs* a, const float2* tw, cudaStream_t st) {
   constexpr bool IO = PREC == 0 && !mixed_len(LX);
   prep(row_kernel<LX, RB, PREC>, SOK ? row_stage_smem<LX, RB>() : smem);
   if (!a) {
-    if constexpr (IO) row_io_dispatch(LX, RB, nullptr, nullptr, nullptr);
+    if constexpr (IO) {
+      row_io_dispatch(LX, RB, nullptr, nullptr, nullptr);
+      row_rk_dispatch(LX, RB, nullptr, nullptr, nullptr);
+    }
     return;
   }
   RowArgs b = *a;
   b.stage = SOK && row_stage_applies(b);
   if constexpr (IO) {
     if ((b.mode == ROW_FWD || (b.mode == ROW_H && !b.extrap)) && row_io_dispatch(LX, RB, &b, tw, st)) return;
+    // staged RK stages whose blocks each lie in one z plane take the KIND 2 instances (gbd_row_rk.cu)
+    if (b.stage && b.ny % RB == 0 && b.ny % 2 == 0 && row_rk_dispatch(LX, RB, &b, tw, st)) return;
   }
   launch_pdl(row_kernel<LX, RB, PREC>, (b.rows + RB - 1) / RB, T, b.stage ? row_stage_smem<LX, RB>() : smem, st, b, tw);
 }
